@@ -1,0 +1,409 @@
+"""Benchmark: batched HighwayHash-64 on GB300 (arXiv:1612.06257, Section 4).
+
+One step = one pass of the whole hash path (Init, packet Updates, remainder,
+four finalisation rounds, output) over one batch of 2^20 messages of 1024
+uniform random bytes (1 GiB) with one 256-bit key, through libhh's C ABI.
+The inputs (1 GiB) are larger than L2 (129 MB), so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Rank 0 prints one JSON line.  --impl reference times the CPU oracle (the
+scalar C implementation the tests check against) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("GB/s hashed and hashes/s per GB300 vs HBM/integer roofline; "
+          "p50/p99 request latency")
+N_MESSAGES = 1 << 20
+MESSAGE_BYTES = 1024
+WORKLOAD = ("HighwayHash-64, 2^20 messages x 1024 B of uniform random bytes (1 GiB), "
+            "one random 256-bit key, fixed-length contiguous batch, uint64 out")
+OUT_BYTES = 8
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """Samples SM clock and clock-event reasons through NVML in a thread."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+               0x2: "applications_clocks_setting", 0x100: "display_clock_setting"}
+
+    def __init__(self, torch_device: int, period_s: float = 0.005):
+        import torch
+        self.period = period_s
+        self.samples = []
+        self.ok = False
+        self._stop = threading.Event()
+        try:
+            self.nvml = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nvml.nvmlInit_v2() != 0:
+                return
+            self.handle = ctypes.c_void_p()
+            uuid = getattr(torch.cuda.get_device_properties(torch_device), "uuid", None)
+            rc = 1
+            if uuid is not None:
+                s = str(uuid)
+                s = s if s.startswith("GPU-") else "GPU-" + s
+                rc = self.nvml.nvmlDeviceGetHandleByUUID(s.encode(), ctypes.byref(self.handle))
+            if rc != 0:
+                rc = self.nvml.nvmlDeviceGetHandleByIndex_v2(torch_device, ctypes.byref(self.handle))
+            if rc != 0:
+                return
+            mx = ctypes.c_uint()
+            self.nvml.nvmlDeviceGetMaxClockInfo(self.handle, 1, ctypes.byref(mx))
+            self.max_mhz = int(mx.value)
+            self.ok = True
+        except OSError:
+            self.ok = False
+
+    def _read(self):
+        mhz = ctypes.c_uint()
+        reasons = ctypes.c_ulonglong()
+        self.nvml.nvmlDeviceGetClockInfo(self.handle, 1, ctypes.byref(mhz))
+        fn = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nvml.nvmlDeviceGetCurrentClocksThrottleReasons
+        fn(self.handle, ctypes.byref(reasons))
+        return int(mhz.value), int(reasons.value)
+
+    def _loop(self):
+        while not self._stop.is_set():
+            self.samples.append(self._read())
+            time.sleep(self.period)
+
+    def start(self):
+        if self.ok:
+            self.thread = threading.Thread(target=self._loop, daemon=True)
+            self.thread.start()
+
+    def stop(self):
+        if self.ok:
+            self._stop.set()
+            self.thread.join()
+            self.samples.append(self._read())
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        mhz = [m for m, _ in self.samples]
+        mask = 0
+        for _, r in self.samples:
+            mask |= r
+        names = sorted(v for k, v in self.REASONS.items() if mask & k)
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": self.max_mhz,
+                "reasons": names, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_digest() -> str:
+    csrc = os.path.join(ROOT, "paper_1612_06257_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic_per_launch(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_digest") != kernel_source_digest():
+        return None
+    return float(rec["dram_bytes_per_launch"])
+
+
+def oracle_rate(keys, data, offsets, first, count, threads):
+    """Hash messages [first, first+count) with the oracle on `threads` host
+    threads; returns (seconds, hashes)."""
+    import oracle
+    n = count
+    out = np.zeros((n, 1), dtype=np.uint64)
+    step = max(1, (n + threads - 1) // threads)
+
+    def run(a):
+        b = min(n, a + step)
+        oracle.hash_batch(keys, False, data, offsets, 64, first + a, first + b, out[a:b])
+
+    t0 = time.perf_counter()
+    with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(run, range(0, n, step)))
+    return time.perf_counter() - t0, out
+
+
+def cpu_baseline(keys, data, offsets, n_total, target_wall_s=1.5):
+    """The oracle as it stands, on all host cores, on a bounded sample."""
+    cores = os.cpu_count() or 1
+    probe = 64
+    t, _ = oracle_rate(keys, data, offsets, 0, probe, 1)
+    per_core_bps = probe * MESSAGE_BYTES / max(t, 1e-9)
+    count = int(per_core_bps * cores * target_wall_s / MESSAGE_BYTES)
+    count = max(cores * 16, min(count, n_total))
+    secs, out = oracle_rate(keys, data, offsets, 0, count, cores)
+    gbps = count * MESSAGE_BYTES / secs / 1e9
+    return {"value": round(gbps, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d of the 2^20 x 1 KiB messages (%.1f MiB), %d threads, %.2f s wall"
+                      % (count, count * MESSAGE_BYTES / 2**20, cores, secs),
+            "hashes_per_s": round(count / secs, 1)}, out, count
+
+
+# --------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1612_06257_gb300 import build, hh, workloads
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    ctx = hh.hh_init(local_rank)
+    w = workloads.fixed(N_MESSAGES, MESSAGE_BYTES, seed=1000 + rank, device=dev)
+    out = torch.empty(N_MESSAGES, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(bits=64, o=out):
+        hh.hh_hash_fixed(ctx, bits, w.keys, 0, w.data, MESSAGE_BYTES, N_MESSAGES, out=o,
+                         stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    launches_per_step = hh.hh_last_launch_count(ctx)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    sampler = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    region0 = torch.cuda.Event(enable_timing=True)
+    region1 = torch.cuda.Event(enable_timing=True)
+    region0.record(stream)
+    for i in range(K):
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    region1.record(stream)
+    torch.cuda.synchronize()
+    sampler.stop()
+    if dist:
+        dist.barrier()
+    region_ms = region0.elapsed_time(region1)
+    launch_ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if dist:
+        t = torch.tensor([region_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        region_ms = float(t.item())
+    status = hh.hh_get_device_error(ctx)
+    if status != hh.HH_OK:
+        raise RuntimeError("device error during the benchmark: " + hh.hh_status_string(status))
+
+    ms_per_step = region_ms / K
+    payload = N_MESSAGES * MESSAGE_BYTES
+    value = world * payload / (ms_per_step / 1e3) / 1e9
+    hashes_per_s = world * N_MESSAGES / (ms_per_step / 1e3)
+
+    # Roofline of the one kernel each step launches (the staged, 16-byte
+    # aligned variant): algorithmic bytes = payload read once + 8-byte output
+    # per message (the fixed-length form reads no offsets).
+    alg_bytes = N_MESSAGES * (MESSAGE_BYTES + OUT_BYTES) + 32
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    kernel_name = "staged_kernel<128,3,aligned>"
+    traffic = dram_traffic_per_launch(kernel_name)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy burst)",
+                "kernel": kernel_name, "algorithmic_bytes_per_launch": alg_bytes,
+                "launch_ms": round(launch_ms, 4)}
+
+    extra = {}
+    # Other output widths and the plain one-message-per-thread kernel, timed
+    # on the same batch after the main region (a few steps each).
+    reps = max(3, min(K, 20))
+    for bits in (128, 256):
+        o = torch.empty(N_MESSAGES * bits // 64, dtype=torch.int64, device=dev)
+        step(bits, o)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            step(bits, o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        extra["gbps_%d" % bits] = round(payload / (e0.elapsed_time(e1) / reps / 1e3) / 1e9, 1)
+    hh.hh_set_kernel(ctx, hh.HH_KERNEL_NAIVE)
+    step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    hh.hh_set_kernel(ctx, hh.HH_KERNEL_AUTO)
+    naive_gbps = payload / (e0.elapsed_time(e1) / reps / 1e3) / 1e9
+    extra["naive_gbps"] = round(naive_gbps, 1)
+    extra["speedup_vs_naive"] = round(value / world / naive_gbps, 2)
+
+    # End to end through the host-buffer C ABI call: pinned host inputs, the
+    # H2D copies, hashing and the D2H copy of the hashes inside the region.
+    host_data = torch.empty(payload, dtype=torch.uint8, pin_memory=True)
+    host_data.copy_(w.data)
+    host_offsets = (np.arange(N_MESSAGES + 1, dtype=np.int64) * MESSAGE_BYTES)
+    host_keys = w.keys.cpu().numpy().view(np.uint64).copy()
+    host_out = torch.empty(N_MESSAGES, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    hd = host_data.numpy()
+    hh.hh_hash_host(ctx, 64, host_keys, 0, hd, host_offsets, out=host_out)
+    e2e_steps = max(3, min(K, 20))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        hh.hh_hash_host(ctx, 64, host_keys, 0, hd, host_offsets, out=host_out)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": round(world * payload / e2e_s / 1e9, 2), "unit": "GB/s",
+           "h2d_bytes_per_step": payload + 8 * (N_MESSAGES + 1) + 32,
+           "d2h_bytes_per_step": 8 * N_MESSAGES,
+           "api": "hh_hash_host (pinned host buffers, chunked H2D/hash/D2H)"}
+
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded uniform random bytes and key, generated on device)",
+        "config": {"workload": WORKLOAD, "n_messages": N_MESSAGES,
+                   "message_bytes": MESSAGE_BYTES, "bits": 64, "key": "shared",
+                   "api": "hh_hash_fixed", "l2": "inputs (1 GiB) larger than L2 (129 MB); no flush",
+                   "parallelism": "replica per GPU" if world > 1 else "single GPU"},
+        "hashes_per_s": round(hashes_per_s, 1),
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": K * launches_per_step,
+        "clocks": sampler.summary(),
+        "extra": extra,
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        keys_np = w.keys.cpu().numpy().view(np.uint64)
+        sample_msgs = min(N_MESSAGES, 1 << 18)
+        data_np = w.data[: sample_msgs * MESSAGE_BYTES].cpu().numpy()
+        offs_np = np.arange(sample_msgs + 1, dtype=np.int64) * MESSAGE_BYTES
+        base, ref_out, count = cpu_baseline(keys_np, data_np, offs_np, sample_msgs)
+        gpu_out = out[:count].cpu().numpy().view(np.uint64)
+        base["matches_gpu"] = bool(np.array_equal(gpu_out, ref_out[:, 0]))
+        result["cpu_baseline"] = base
+    hh.hh_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+    return result
+
+
+# -------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    """The CPU oracle on the host cores; each step hashes a bounded sample of
+    the same workload (4096 of the 1 KiB messages, 4 MiB)."""
+    if rank != 0:
+        return None
+    import torch
+    from paper_1612_06257_gb300 import workloads
+    g_msgs = 4096
+    w = workloads.fixed(g_msgs, MESSAGE_BYTES, seed=1000, device="cpu")
+    keys = w.keys.numpy().view(np.uint64)
+    data = w.data.numpy()
+    offs = np.arange(g_msgs + 1, dtype=np.int64) * MESSAGE_BYTES
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_rate(keys, data, offs, 0, g_msgs, cores)
+    times = []
+    for _ in range(args.steps):
+        t, _ = oracle_rate(keys, data, offs, 0, g_msgs, cores)
+        times.append(t)
+    sec = statistics.mean(times)
+    value = g_msgs * MESSAGE_BYTES / sec / 1e9
+    del torch
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded, host)",
+        "config": {"workload": WORKLOAD, "n_messages": N_MESSAGES,
+                   "message_bytes": MESSAGE_BYTES, "bits": 64, "key": "shared"},
+        "hashes_per_s": round(g_msgs / sec, 1),
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": "each step: %d of the 1 KiB messages (%d MiB) on %d threads"
+                                   % (g_msgs, g_msgs * MESSAGE_BYTES >> 20, cores)},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_ours(args, rank, world, local_rank)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

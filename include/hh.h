@@ -1,0 +1,178 @@
+/*
+ * hh.h -- C ABI of libhh, a batched HighwayHash engine for NVIDIA GB300 (sm_103a).
+ *
+ * HighwayHash is the keyed pseudo-random function of Alakuijala, Cox and
+ * Wassenberg, "Fast keyed hash/pseudo-random function using SIMD multiply and
+ * permute" (arXiv:1612.06257).  A 256-bit key and a message of any length map
+ * to a 64-, 128- or 256-bit hash (Sections 1 and 4.3).  Per message the
+ * library runs, entirely in its own CUDA kernels:
+ *   Init from the key (Section 4.4) -> one Update per whole 32-byte packet
+ *   (Section 4.2, with ZipperMerge of Section 4.1) -> size injection and one
+ *   padded Update of the last size mod 32 bytes (Section 4.5) -> four rounds
+ *   of Update(Permute(v0)) (Section 4.3) -> h[i] = v0[i]+v1[i]+mul0[i]+mul1[i].
+ * The 64-bit hash is h[0], the 128-bit hash (h[0], h[1]), the 256-bit hash
+ * h[0..3].  Every message is independent.
+ *
+ * Details the paper leaves open are fixed as follows: packets and keys are
+ * little-endian 64-bit lanes, lane 0 first; the size mod 32 is added to each
+ * lane of v0 as one 64-bit add of (r << 32) + r; v1's 32-bit halves are
+ * rotated left by r; the last r mod 4 bytes go to packet bytes 28..30; the
+ * initialisation constants take pi's first hex words most-significant lane
+ * first.  Agreement with any released HighwayHash library is not claimed.
+ *
+ * Conventions for every call below:
+ *  - Unless a function says "host", every pointer is a DEVICE pointer (memory
+ *    from cudaMalloc, cudaMallocAsync or a caching allocator on the context's
+ *    device).  The caller owns all buffers; they must stay valid until the
+ *    work queued on `stream` has finished.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Hash calls are asynchronous: they enqueue work and
+ *    return; results are ready when the stream reaches that point.
+ *  - Errors the host can detect (null pointers, bad sizes, bad modes) are
+ *    returned synchronously and nothing is enqueued.  Errors only the device
+ *    can see (decreasing offsets, a pipeline wait that ran out) are recorded
+ *    in a per-context device error word; read it with hh_get_device_error.
+ *    No call aborts, throws or prints.
+ *  - One hh_ctx may be used by one host thread at a time.  Calls on one
+ *    context from several threads need external locking.  Concurrent calls
+ *    on different streams of one context share its scratch memory and must
+ *    not overlap on the device.
+ */
+#ifndef HH_H
+#define HH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hh_ctx hh_ctx;
+
+/* Status codes returned by every call. */
+enum hh_status {
+  HH_OK = 0,
+  HH_ERR_INVALID_ARG = 1,   /* null pointer with n > 0, bad mode, bad bits   */
+  HH_ERR_CUDA = 2,          /* a CUDA runtime call failed                     */
+  HH_ERR_NO_MEMORY = 3,     /* device or host allocation failed               */
+  HH_ERR_TIMEOUT = 4,       /* device: a bounded pipeline wait ran out        */
+  HH_ERR_TOO_LARGE = 5,     /* a size beyond what the call supports           */
+  HH_ERR_BAD_OFFSETS = 6,   /* device: offsets[i+1] < offsets[i] somewhere    */
+  HH_ERR_NO_DEVICE = 7      /* no usable CUDA device with sm_103a             */
+};
+
+/* How `keys` is laid out. */
+enum hh_key_mode {
+  HH_KEY_SHARED = 0,        /* keys = uint64[4]: one key for every message    */
+  HH_KEY_PER_MESSAGE = 1    /* keys = uint64[n][4]: key of message i at 4*i   */
+};
+
+/* Kernel choice (for benchmarking and tests; HH_KERNEL_AUTO is the product
+ * default and picks the staged kernels). */
+enum hh_kernel {
+  HH_KERNEL_AUTO = 0,
+  HH_KERNEL_NAIVE = 1,      /* one thread per message, direct global loads    */
+  HH_KERNEL_STAGED = 2,     /* length-sorted, shared-memory staged (bulk copy) */
+  HH_KERNEL_STAGED_UNSORTED = 3 /* staged, messages taken in index order      */
+};
+
+/*
+ * Create a context on CUDA device `device`.  It owns a small device error
+ * word, a work-queue counter and scratch memory for the length sort, which
+ * grows when a call needs more (see hh_reserve).  `tune_cache_path` is
+ * reserved for a tuning table and must be NULL.
+ * Returns HH_ERR_NO_DEVICE when the device is absent or not sm_103a.
+ * The caller's current device is restored before returning.
+ */
+int hh_init(hh_ctx** out, int device, const char* tune_cache_path);
+
+/* Free everything the context owns.  Waits for its device work first.
+ * NULL is accepted and ignored. */
+int hh_destroy(hh_ctx* ctx);
+
+/*
+ * Pre-allocate scratch for batches of up to `max_messages` messages, so that
+ * later calls of that size allocate nothing (and can be captured into a CUDA
+ * graph).  A hash call with more messages grows the scratch itself, which
+ * synchronises the device; inside a stream capture it returns
+ * HH_ERR_TOO_LARGE instead.
+ */
+int hh_reserve(hh_ctx* ctx, int64_t max_messages);
+
+/*
+ * Hash a ragged batch (Sections 4.2-4.5).
+ *   keys     per key_mode: uint64[4] or uint64[n][4], little-endian lanes.
+ *   bytes    concatenated message bytes; message i is
+ *            bytes[offsets[i] .. offsets[i+1]).  No alignment requirement;
+ *            must not be NULL when n > 0.
+ *            The library reads only bytes in [offsets[0], offsets[n]).
+ *   offsets  int64[n+1], non-decreasing, offsets[0] >= 0.  A decreasing pair
+ *            sets HH_ERR_BAD_OFFSETS on the device and that message's output
+ *            words are written as zero.
+ *   n        number of messages; n == 0 is a no-op returning HH_OK.
+ *   out      uint64[n * words] with words = 1, 2, 4 for 64/128/256 bits;
+ *            message i's hash is out[words*i .. words*i + words).
+ * Returns HH_OK once the work is enqueued on `stream`.
+ */
+int hh_hash64_batch(hh_ctx* ctx, const uint64_t* keys, int key_mode, const uint8_t* bytes,
+                    const int64_t* offsets, int64_t n, uint64_t* out, void* stream);
+int hh_hash128_batch(hh_ctx* ctx, const uint64_t* keys, int key_mode, const uint8_t* bytes,
+                     const int64_t* offsets, int64_t n, uint64_t* out, void* stream);
+int hh_hash256_batch(hh_ctx* ctx, const uint64_t* keys, int key_mode, const uint8_t* bytes,
+                     const int64_t* offsets, int64_t n, uint64_t* out, void* stream);
+
+/*
+ * Hash a fixed-length batch: message i is bytes[i*msg_len .. (i+1)*msg_len).
+ * Same semantics as the ragged calls without the offsets array.  bits is 64,
+ * 128 or 256.  bytes may be NULL only when msg_len == 0.  When bytes is
+ * 16-byte aligned and msg_len a multiple of 16, a kernel that needs no
+ * realignment runs.
+ */
+int hh_hash_fixed(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
+                  const uint8_t* bytes, int64_t msg_len, int64_t n, uint64_t* out,
+                  void* stream);
+
+/*
+ * Host-memory variant of the ragged call: keys, bytes, offsets and out are
+ * HOST pointers (pinned memory gives full copy speed; pageable works).  The
+ * batch is copied to the device in chunks, hashed there and copied back,
+ * with copies and hashing of consecutive chunks overlapped.  Synchronous:
+ * returns after `out` is filled.  Device staging memory is owned by the
+ * context and grows on first use.  bits is 64, 128 or 256.
+ */
+int hh_hash_host(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
+                 const uint8_t* bytes, const int64_t* offsets, int64_t n, uint64_t* out);
+
+/*
+ * Synchronise `stream`, then return and clear the context's device error
+ * word: HH_OK, HH_ERR_BAD_OFFSETS or HH_ERR_TIMEOUT (the first one recorded).
+ */
+int hh_get_device_error(hh_ctx* ctx, void* stream);
+
+/* Force one kernel family (enum hh_kernel) for later calls on ctx. */
+int hh_set_kernel(hh_ctx* ctx, int kernel);
+
+/* Batch regimes that have their own staged-kernel shape. */
+enum hh_regime {
+  HH_REGIME_FIXED = 0,      /* hh_hash_fixed                                  */
+  HH_REGIME_RAGGED = 1      /* the offsets-based calls                        */
+};
+
+/* Set the staged kernel's shape for one regime: `window` bytes of every
+ * message staged per pipeline step and `stages` pipeline buffers.  Supported
+ * (window, stages): (128, 3), (128, 4), (256, 2), (256, 3).  Other pairs
+ * return HH_ERR_INVALID_ARG. */
+int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages);
+
+/* Number of kernel launches the last hash call on ctx enqueued. */
+int hh_last_launch_count(hh_ctx* ctx);
+
+/* A static, human-readable description of a status code. */
+const char* hh_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HH_H */

@@ -1,0 +1,413 @@
+// hh_api.cu -- the C ABI of libhh (declared in include/hh.h).
+//
+// Host-side only: argument checks, kernel choice, scratch memory for the
+// length sort, and the chunked host-buffer path.  Every step of the hash
+// itself runs in the kernels of hh_kernels.cu and hh_bucket.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "hh.h"
+#include "hh_internal.h"
+
+namespace {
+
+constexpr int64_t kSortMinMessages = 1024;        // below this, index order is fine
+constexpr int64_t kMaxSortedMessages = 0x7FFFFFFFll;
+constexpr size_t kHostChunkBytes = size_t(64) << 20;  // payload per host-path chunk
+constexpr int64_t kHostChunkMessages = int64_t(1) << 20;
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+struct HostSlot {
+  uint8_t* bytes = nullptr;
+  size_t bytes_cap = 0;
+  int64_t* offsets = nullptr;
+  size_t offsets_cap = 0;  // elements
+  uint64_t* keys = nullptr;
+  size_t keys_cap = 0;     // elements
+  uint64_t* out = nullptr;
+  size_t out_cap = 0;      // elements
+  cudaEvent_t staged = nullptr;  // inputs on the device
+  cudaEvent_t hashed = nullptr;  // kernel done
+  cudaEvent_t drained = nullptr; // output copied back: slot reusable
+};
+
+}  // namespace
+
+struct hh_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int kernel = HH_KERNEL_AUTO;
+  int* d_err = nullptr;
+  unsigned long long* d_next_tile = nullptr;
+  uint32_t* d_hist = nullptr;
+  uint32_t* d_cursor = nullptr;
+  int32_t* d_perm = nullptr;
+  int64_t perm_cap = 0;
+  hh::StagedShape shape_ragged{128, 3};
+  hh::StagedShape shape_fixed{128, 3};
+  int last_launches = 0;
+  // Host-buffer path.
+  cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
+  HostSlot slots[2];
+};
+
+namespace {
+
+int to_status(cudaError_t e) {
+  if (e == cudaSuccess) return HH_OK;
+  if (e == cudaErrorMemoryAllocation) return HH_ERR_NO_MEMORY;
+  return HH_ERR_CUDA;
+}
+
+bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+  return st != cudaStreamCaptureStatusNone;
+}
+
+int ensure_perm(hh_ctx* ctx, int64_t n, cudaStream_t stream) {
+  if (n <= ctx->perm_cap) return HH_OK;
+  if (stream_capturing(stream)) return HH_ERR_TOO_LARGE;
+  if (cudaDeviceSynchronize() != cudaSuccess) return HH_ERR_CUDA;
+  if (ctx->d_perm) cudaFree(ctx->d_perm);
+  ctx->d_perm = nullptr;
+  ctx->perm_cap = 0;
+  if (cudaMalloc(&ctx->d_perm, sizeof(int32_t) * static_cast<size_t>(n)) != cudaSuccess)
+    return HH_ERR_NO_MEMORY;
+  ctx->perm_cap = n;
+  return HH_OK;
+}
+
+int words_of(int bits) { return bits == 64 ? 1 : bits == 128 ? 2 : bits == 256 ? 4 : 0; }
+
+// One device-pointer batch, ragged (offsets != null) or fixed-length.
+int hash_device(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode, const uint8_t* bytes,
+                const int64_t* offsets, int64_t fixed_len, int64_t n, uint64_t* out,
+                cudaStream_t stream) {
+  if (ctx == nullptr) return HH_ERR_INVALID_ARG;
+  const int words = words_of(bits);
+  if (words == 0 || (key_mode != HH_KEY_SHARED && key_mode != HH_KEY_PER_MESSAGE) || n < 0 ||
+      fixed_len < 0)
+    return HH_ERR_INVALID_ARG;
+  ctx->last_launches = 0;
+  if (n == 0) return HH_OK;
+  if (keys == nullptr || out == nullptr) return HH_ERR_INVALID_ARG;
+  // Only a fixed-length batch of empty messages may come without bytes.
+  if (bytes == nullptr && !(offsets == nullptr && fixed_len == 0)) return HH_ERR_INVALID_ARG;
+  if (offsets == nullptr && fixed_len > 0 && n > INT64_MAX / fixed_len) return HH_ERR_TOO_LARGE;
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return HH_ERR_CUDA;
+
+  hh::Batch b{};
+  b.bytes = bytes;
+  b.offsets = offsets;
+  b.fixed_len = fixed_len;
+  b.keys = keys;
+  b.per_message_keys = key_mode == HH_KEY_PER_MESSAGE;
+  b.n = n;
+  b.out = out;
+  b.words = words;
+  b.err = ctx->d_err;
+
+  if (ctx->kernel == HH_KERNEL_NAIVE) {
+    ctx->last_launches = 1;
+    return to_status(hh::launch_naive(b, stream));
+  }
+
+  hh::Queue q{};
+  q.tiles = (n + hh::kTileRows - 1) / hh::kTileRows;
+  bool aligned16 = false;
+  hh::StagedShape shape = ctx->shape_ragged;
+  if (offsets == nullptr) {
+    aligned16 = (reinterpret_cast<uintptr_t>(bytes) % 16 == 0) && (fixed_len % 16 == 0);
+    shape = ctx->shape_fixed;
+  } else if (ctx->kernel != HH_KERNEL_STAGED_UNSORTED && n >= kSortMinMessages) {
+    if (n > kMaxSortedMessages) return HH_ERR_TOO_LARGE;
+    int st = ensure_perm(ctx, n, stream);
+    if (st != HH_OK) return st;
+    int launches = 0;
+    cudaError_t e = hh::launch_bucket_sort(offsets, n, ctx->d_hist, ctx->d_cursor, ctx->d_perm,
+                                           ctx->d_next_tile, ctx->num_sms, stream, &launches);
+    ctx->last_launches += launches;
+    if (e != cudaSuccess) return to_status(e);
+    q.perm = ctx->d_perm;
+    q.next_tile = ctx->d_next_tile;
+  }
+  cudaError_t e = hh::launch_staged(b, q, shape, aligned16, ctx->num_sms, stream);
+  ctx->last_launches += 1;
+  return to_status(e);
+}
+
+template <typename T>
+int grow(T** p, size_t* cap, size_t need) {
+  if (need <= *cap) return HH_OK;
+  const size_t want = std::max(need, *cap + *cap / 2);
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(reinterpret_cast<void**>(p), want * sizeof(T)) != cudaSuccess) return HH_ERR_NO_MEMORY;
+  *cap = want;
+  return HH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hh_status_string(int status) {
+  switch (status) {
+    case HH_OK: return "ok";
+    case HH_ERR_INVALID_ARG: return "invalid argument";
+    case HH_ERR_CUDA: return "CUDA runtime error";
+    case HH_ERR_NO_MEMORY: return "out of memory";
+    case HH_ERR_TIMEOUT: return "device pipeline wait timed out";
+    case HH_ERR_TOO_LARGE: return "size too large for this call";
+    case HH_ERR_BAD_OFFSETS: return "offsets decrease";
+    case HH_ERR_NO_DEVICE: return "no usable sm_103 CUDA device";
+    default: return "unknown status";
+  }
+}
+
+int hh_init(hh_ctx** out, int device, const char* tune_cache_path) {
+  (void)tune_cache_path;
+  if (out == nullptr) return HH_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return HH_ERR_NO_DEVICE;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return HH_ERR_NO_DEVICE;
+  if (prop.major != 10 || prop.minor != 3) return HH_ERR_NO_DEVICE;
+  DeviceGuard guard(device);
+  if (!guard.ok) return HH_ERR_CUDA;
+  hh_ctx* ctx = new (std::nothrow) hh_ctx();
+  if (ctx == nullptr) return HH_ERR_NO_MEMORY;
+  ctx->device = device;
+  ctx->num_sms = prop.multiProcessorCount;
+  bool ok = cudaMalloc(&ctx->d_err, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&ctx->d_next_tile, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc(&ctx->d_hist, sizeof(uint32_t) * hh::kBuckets) == cudaSuccess &&
+            cudaMalloc(&ctx->d_cursor, sizeof(uint32_t) * hh::kBuckets) == cudaSuccess &&
+            cudaMemset(ctx->d_err, 0, sizeof(int)) == cudaSuccess &&
+            cudaMemset(ctx->d_next_tile, 0, sizeof(unsigned long long)) == cudaSuccess;
+  if (!ok) {
+    hh_destroy(ctx);
+    return HH_ERR_NO_MEMORY;
+  }
+  *out = ctx;
+  return HH_OK;
+}
+
+int hh_destroy(hh_ctx* ctx) {
+  if (ctx == nullptr) return HH_OK;
+  DeviceGuard guard(ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(ctx->d_err);
+  cudaFree(ctx->d_next_tile);
+  cudaFree(ctx->d_hist);
+  cudaFree(ctx->d_cursor);
+  cudaFree(ctx->d_perm);
+  for (HostSlot& s : ctx->slots) {
+    cudaFree(s.bytes);
+    cudaFree(s.offsets);
+    cudaFree(s.keys);
+    cudaFree(s.out);
+    if (s.staged) cudaEventDestroy(s.staged);
+    if (s.hashed) cudaEventDestroy(s.hashed);
+    if (s.drained) cudaEventDestroy(s.drained);
+  }
+  if (ctx->s_h2d) cudaStreamDestroy(ctx->s_h2d);
+  if (ctx->s_comp) cudaStreamDestroy(ctx->s_comp);
+  if (ctx->s_d2h) cudaStreamDestroy(ctx->s_d2h);
+  delete ctx;
+  return HH_OK;
+}
+
+int hh_reserve(hh_ctx* ctx, int64_t max_messages) {
+  if (ctx == nullptr || max_messages < 0) return HH_ERR_INVALID_ARG;
+  if (max_messages > kMaxSortedMessages) return HH_ERR_TOO_LARGE;
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return HH_ERR_CUDA;
+  return ensure_perm(ctx, max_messages, nullptr);
+}
+
+int hh_hash64_batch(hh_ctx* ctx, const uint64_t* keys, int key_mode, const uint8_t* bytes,
+                    const int64_t* offsets, int64_t n, uint64_t* out, void* stream) {
+  if (offsets == nullptr && n > 0) return HH_ERR_INVALID_ARG;
+  return hash_device(ctx, 64, keys, key_mode, bytes, offsets, 0, n, out,
+                     static_cast<cudaStream_t>(stream));
+}
+
+int hh_hash128_batch(hh_ctx* ctx, const uint64_t* keys, int key_mode, const uint8_t* bytes,
+                     const int64_t* offsets, int64_t n, uint64_t* out, void* stream) {
+  if (offsets == nullptr && n > 0) return HH_ERR_INVALID_ARG;
+  return hash_device(ctx, 128, keys, key_mode, bytes, offsets, 0, n, out,
+                     static_cast<cudaStream_t>(stream));
+}
+
+int hh_hash256_batch(hh_ctx* ctx, const uint64_t* keys, int key_mode, const uint8_t* bytes,
+                     const int64_t* offsets, int64_t n, uint64_t* out, void* stream) {
+  if (offsets == nullptr && n > 0) return HH_ERR_INVALID_ARG;
+  return hash_device(ctx, 256, keys, key_mode, bytes, offsets, 0, n, out,
+                     static_cast<cudaStream_t>(stream));
+}
+
+int hh_hash_fixed(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
+                  const uint8_t* bytes, int64_t msg_len, int64_t n, uint64_t* out,
+                  void* stream) {
+  if (msg_len < 0) return HH_ERR_INVALID_ARG;
+  return hash_device(ctx, bits, keys, key_mode, bytes, nullptr, msg_len, n, out,
+                     static_cast<cudaStream_t>(stream));
+}
+
+int hh_hash_host(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
+                 const uint8_t* bytes, const int64_t* offsets, int64_t n, uint64_t* out) {
+  if (ctx == nullptr) return HH_ERR_INVALID_ARG;
+  const int words = words_of(bits);
+  if (words == 0 || (key_mode != HH_KEY_SHARED && key_mode != HH_KEY_PER_MESSAGE) || n < 0)
+    return HH_ERR_INVALID_ARG;
+  if (n == 0) return HH_OK;
+  if (keys == nullptr || bytes == nullptr || offsets == nullptr || out == nullptr)
+    return HH_ERR_INVALID_ARG;
+  if (offsets[0] < 0 || offsets[n] < offsets[0]) return HH_ERR_BAD_OFFSETS;
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return HH_ERR_CUDA;
+  if (ctx->s_h2d == nullptr) {
+    if (cudaStreamCreateWithFlags(&ctx->s_h2d, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->s_d2h, cudaStreamNonBlocking) != cudaSuccess)
+      return HH_ERR_CUDA;
+    for (HostSlot& s : ctx->slots) {
+      if (cudaEventCreateWithFlags(&s.staged, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&s.hashed, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&s.drained, cudaEventDisableTiming) != cudaSuccess)
+        return HH_ERR_CUDA;
+    }
+  }
+  // Chunk boundaries: at most kHostChunkMessages messages and (unless a single
+  // message is larger) kHostChunkBytes payload per chunk.
+  int launches = 0;
+  int chunk_index = 0;
+  int64_t m0 = 0;
+  while (m0 < n) {
+    int64_t m1 = m0 + 1;
+    const int64_t limit = std::min<int64_t>(n, m0 + kHostChunkMessages);
+    {
+      // Largest m1 <= limit with offsets[m1] - offsets[m0] <= chunk bytes.
+      int64_t lo = m0 + 1, hi = limit;
+      while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (offsets[mid] - offsets[m0] <= static_cast<int64_t>(kHostChunkBytes)) lo = mid;
+        else hi = mid - 1;
+      }
+      m1 = lo;
+    }
+    if (offsets[m1] < offsets[m0]) return HH_ERR_BAD_OFFSETS;
+    HostSlot& s = ctx->slots[chunk_index & 1];
+    const int64_t cn = m1 - m0;
+    const size_t cbytes = static_cast<size_t>(offsets[m1] - offsets[m0]);
+    // The slot's previous chunk must have drained before its buffers change.
+    if (cudaStreamWaitEvent(ctx->s_h2d, s.drained, 0) != cudaSuccess) return HH_ERR_CUDA;
+    if (cbytes > s.bytes_cap || static_cast<size_t>(cn + 1) > s.offsets_cap ||
+        static_cast<size_t>(cn) * words > s.out_cap ||
+        (key_mode == HH_KEY_PER_MESSAGE && static_cast<size_t>(cn) * 4 > s.keys_cap) ||
+        s.keys_cap < 4) {
+      if (cudaDeviceSynchronize() != cudaSuccess) return HH_ERR_CUDA;
+      int st = grow(&s.bytes, &s.bytes_cap, std::max<size_t>(cbytes, 16));
+      if (st == HH_OK) st = grow(&s.offsets, &s.offsets_cap, static_cast<size_t>(cn + 1));
+      if (st == HH_OK) st = grow(&s.out, &s.out_cap, static_cast<size_t>(cn) * words);
+      if (st == HH_OK)
+        st = grow(&s.keys, &s.keys_cap,
+                  key_mode == HH_KEY_PER_MESSAGE ? static_cast<size_t>(cn) * 4 : size_t(4));
+      if (st != HH_OK) return st;
+    }
+    const uint64_t* ck = key_mode == HH_KEY_PER_MESSAGE ? keys + 4 * m0 : keys;
+    const size_t key_words = key_mode == HH_KEY_PER_MESSAGE ? static_cast<size_t>(cn) * 4 : 4;
+    cudaError_t e = cudaMemcpyAsync(s.bytes, bytes + offsets[m0], cbytes, cudaMemcpyHostToDevice,
+                                    ctx->s_h2d);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s.offsets, offsets + m0, sizeof(int64_t) * (cn + 1),
+                          cudaMemcpyHostToDevice, ctx->s_h2d);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s.keys, ck, sizeof(uint64_t) * key_words, cudaMemcpyHostToDevice,
+                          ctx->s_h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(s.staged, ctx->s_h2d);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_comp, s.staged, 0);
+    if (e != cudaSuccess) return HH_ERR_CUDA;
+    // The device offsets are absolute; shift the base so that
+    // base + offsets[m0] is the first staged byte.
+    const uint8_t* dev_base = s.bytes - offsets[m0];
+    int st = hash_device(ctx, bits, s.keys, key_mode, dev_base, s.offsets, 0, cn, s.out,
+                         ctx->s_comp);
+    launches += ctx->last_launches;
+    if (st != HH_OK) return st;
+    e = cudaEventRecord(s.hashed, ctx->s_comp);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_d2h, s.hashed, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out + m0 * words, s.out, sizeof(uint64_t) * cn * words,
+                          cudaMemcpyDeviceToHost, ctx->s_d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(s.drained, ctx->s_d2h);
+    if (e != cudaSuccess) return HH_ERR_CUDA;
+    m0 = m1;
+    ++chunk_index;
+  }
+  ctx->last_launches = launches;
+  if (cudaStreamSynchronize(ctx->s_d2h) != cudaSuccess) return HH_ERR_CUDA;
+  int err = 0;
+  if (cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HH_ERR_CUDA;
+  if (err != 0) {
+    cudaMemset(ctx->d_err, 0, sizeof(int));
+    return err;
+  }
+  return HH_OK;
+}
+
+int hh_get_device_error(hh_ctx* ctx, void* stream) {
+  if (ctx == nullptr) return HH_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return HH_ERR_CUDA;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return HH_ERR_CUDA;
+  int err = 0;
+  if (cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HH_ERR_CUDA;
+  if (err != 0 && cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) return HH_ERR_CUDA;
+  return err;
+}
+
+int hh_set_kernel(hh_ctx* ctx, int kernel) {
+  if (ctx == nullptr || kernel < HH_KERNEL_AUTO || kernel > HH_KERNEL_STAGED_UNSORTED)
+    return HH_ERR_INVALID_ARG;
+  ctx->kernel = kernel;
+  return HH_OK;
+}
+
+int hh_last_launch_count(hh_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages) {
+  if (ctx == nullptr || (regime != HH_REGIME_FIXED && regime != HH_REGIME_RAGGED))
+    return HH_ERR_INVALID_ARG;
+  const hh::StagedShape shape{window, stages};
+  if (hh::staged_smem_bytes(shape) == 0) return HH_ERR_INVALID_ARG;
+  if (regime == HH_REGIME_FIXED) ctx->shape_fixed = shape;
+  else ctx->shape_ragged = shape;
+  return HH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,160 @@
+// hh_bucket.cu -- length bucketing of a ragged batch (work-queue order).
+//
+// A message of length L needs ceil(L / 32) Updates before finalisation (one
+// per whole 32-byte packet plus one for a partial packet, Sections 4.2 and
+// 4.5).  Messages are counting-sorted by that number, capped at kBuckets - 1,
+// in DESCENDING order, so that each 128-message tile of the staged kernel
+// holds messages of nearly equal length (no warp waits on one long message)
+// and tiles are handed out longest first (the long ones cannot end up last).
+//
+// Three kernels: per-block histograms merged with one global atomic per
+// non-empty bucket; a one-block exclusive scan in descending bucket order
+// (which also resets the tile counter of the work queue); and a scatter that
+// ranks elements inside each 8192-element chunk in shared memory and reserves
+// each bucket's range with one global atomic per chunk.  The order inside a
+// bucket depends on atomic timing; results do not, because every message's
+// hash is stored at its own index.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hh_internal.h"
+
+namespace hh {
+namespace {
+
+constexpr int kSortThreads = 1024;
+constexpr int kPerThread = 8;
+constexpr int kChunk = kSortThreads * kPerThread;
+
+__device__ __forceinline__ int bucket_of(const int64_t* offsets, int64_t i) {
+  const int64_t len = offsets[i + 1] - offsets[i];
+  if (len <= 0) return 0;  // empty, or invalid (reported by the hash kernel)
+  const int64_t k = (len + 31) >> 5;
+  return k >= kBuckets ? kBuckets - 1 : static_cast<int>(k);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__global__ void __launch_bounds__(kSortThreads) bucket_count_kernel(const int64_t* offsets,
+                                                                    int64_t n, uint32_t* hist) {
+  __shared__ uint32_t h[kBuckets];
+  for (int i = threadIdx.x; i < kBuckets; i += kSortThreads) h[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int64_t c = static_cast<int64_t>(blockIdx.x) * kChunk; c < n;
+       c += static_cast<int64_t>(gridDim.x) * kChunk) {
+#pragma unroll
+    for (int e = 0; e < kPerThread; ++e) {
+      const int64_t i = c + e * kSortThreads + threadIdx.x;
+      const int key = i < n ? bucket_of(offsets, i) : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[key], __popc(peers));
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBuckets; i += kSortThreads)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// cursor[k] = number of messages in buckets above k (descending order).
+__global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_t* hist,
+                                                                   uint32_t* cursor,
+                                                                   unsigned long long* next_tile) {
+  constexpr int kPer = kBuckets / kSortThreads;  // 4 buckets per thread
+  __shared__ uint32_t warp_sums[kSortThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // Thread tid owns descending positions tid*kPer .. tid*kPer + kPer - 1,
+  // i.e. buckets kBuckets-1-pos.
+  uint32_t v[kPer];
+  uint32_t local = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    v[j] = hist[kBuckets - 1 - (tid * kPer + j)];
+    local += v[j];
+  }
+  uint32_t incl = local;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += x;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = warp_sums[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += x;
+    }
+    warp_sums[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  uint32_t run = incl - local + (warp > 0 ? warp_sums[warp - 1] : 0u);
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    cursor[kBuckets - 1 - (tid * kPer + j)] = run;
+    run += v[j];
+  }
+  if (tid == 0) *next_tile = 0ull;
+}
+
+__global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(const int64_t* offsets,
+                                                                      int64_t n, uint32_t* cursor,
+                                                                      int32_t* perm) {
+  __shared__ uint32_t cnt[kBuckets];
+  __shared__ uint32_t base[kBuckets];
+  const int lane = threadIdx.x & 31;
+  for (int64_t c = static_cast<int64_t>(blockIdx.x) * kChunk; c < n;
+       c += static_cast<int64_t>(gridDim.x) * kChunk) {
+    for (int i = threadIdx.x; i < kBuckets; i += kSortThreads) cnt[i] = 0;
+    __syncthreads();
+    int key[kPerThread];
+    uint32_t rank[kPerThread];
+#pragma unroll
+    for (int e = 0; e < kPerThread; ++e) {
+      const int64_t i = c + e * kSortThreads + threadIdx.x;
+      key[e] = i < n ? bucket_of(offsets, i) : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, key[e]);
+      const int leader = __ffs(peers) - 1;
+      uint32_t first = 0;
+      if (key[e] >= 0 && lane == leader) first = atomicAdd(&cnt[key[e]], __popc(peers));
+      first = __shfl_sync(0xffffffffu, first, leader);
+      rank[e] = first + __popc(peers & lanemask_lt());
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBuckets; i += kSortThreads)
+      if (cnt[i]) base[i] = atomicAdd(&cursor[i], cnt[i]);
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < kPerThread; ++e) {
+      const int64_t i = c + e * kSortThreads + threadIdx.x;
+      if (key[e] >= 0) perm[base[key[e]] + rank[e]] = static_cast<int32_t>(i);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_bucket_sort(const int64_t* offsets, int64_t n, uint32_t* hist,
+                               uint32_t* cursor, int32_t* perm, unsigned long long* next_tile,
+                               int num_sms, cudaStream_t stream, int* launches) {
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kBuckets, stream);
+  if (e != cudaSuccess) return e;
+  const int64_t chunks = (n + kChunk - 1) / kChunk;
+  const int64_t cap = static_cast<int64_t>(num_sms) * 2;
+  const int grid = static_cast<int>(chunks < cap ? chunks : cap);
+  bucket_count_kernel<<<grid, kSortThreads, 0, stream>>>(offsets, n, hist);
+  bucket_scan_kernel<<<1, kSortThreads, 0, stream>>>(hist, cursor, next_tile);
+  bucket_scatter_kernel<<<grid, kSortThreads, 0, stream>>>(offsets, n, cursor, perm);
+  *launches += 3;
+  return cudaGetLastError();
+}
+
+}  // namespace hh

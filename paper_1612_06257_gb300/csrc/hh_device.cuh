@@ -1,0 +1,154 @@
+// hh_device.cuh -- per-message HighwayHash arithmetic for sm_103a.
+//
+// HighwayHash (arXiv:1612.06257, Section 4) keeps a 1024-bit state per
+// message in registers: four vectors v0, v1, mul0, mul1 of four 64-bit lanes
+// (Section 4.2).  All arithmetic is exact modulo 2^64; the 32x32->64-bit
+// multiply compiles to IMAD.WIDE.U32 and ZipperMerge to six PRMT (byte_perm)
+// per lane pair.  Nothing here is shared with the CPU checker.
+#pragma once
+
+#include <cstdint>
+
+namespace hh {
+
+// ---------------------------------------------------------------- Section 4.4
+// The first eight 64-bit words of pi's hexadecimal fraction (3.243F6A88...).
+// Words 0-3 give the first constant, words 4-7 the second.  Written most
+// significant lane first, so word 0 is lane 3 and the "fourth number" lane 0;
+// lane 0 then gets every bit that fewer than two of the other lanes have.
+// (A function rather than a table: device code cannot read a host array.)
+__host__ __device__ constexpr uint64_t pi_frac(int i) {
+  return i == 0 ? 0x243F6A8885A308D3ull : i == 1 ? 0x13198A2E03707344ull
+       : i == 2 ? 0xA4093822299F31D0ull : i == 3 ? 0x082EFA98EC4E6C89ull
+       : i == 4 ? 0x452821E638D01377ull : i == 5 ? 0xBE5466CF34E90C6Cull
+       : i == 6 ? 0xC0AC29B7C97C50DDull : 0x3F84D5B5B5470917ull;
+}
+
+__host__ __device__ constexpr uint64_t at_least_two_of(uint64_t a, uint64_t b, uint64_t c) {
+  return (a & b) | (c & (a | b));
+}
+
+__host__ __device__ constexpr uint64_t init_lane(int which, int lane) {
+  return lane == 3 ? pi_frac(4 * which + 0)
+       : lane == 2 ? pi_frac(4 * which + 1)
+       : lane == 1 ? pi_frac(4 * which + 2)
+                   : pi_frac(4 * which + 3) |
+                         ~at_least_two_of(pi_frac(4 * which), pi_frac(4 * which + 1),
+                                          pi_frac(4 * which + 2));
+}
+
+struct State {
+  uint64_t v0[4], v1[4], mul0[4], mul1[4];
+};
+
+__device__ __forceinline__ uint32_t lo32(uint64_t x) { return static_cast<uint32_t>(x); }
+__device__ __forceinline__ uint32_t hi32(uint64_t x) { return static_cast<uint32_t>(x >> 32); }
+__device__ __forceinline__ uint64_t join(uint32_t lo, uint32_t hi) {
+  return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+__device__ __forceinline__ uint64_t swap_halves(uint64_t x) { return join(hi32(x), lo32(x)); }
+
+// Section 4.4: v0 = key ^ C0, v1 = (key, 32-bit halves swapped) ^ C1,
+// mul0 = C0, mul1 = C1.
+__device__ __forceinline__ void init(State& s, const uint64_t key[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint64_t c0 = init_lane(0, i), c1 = init_lane(1, i);
+    s.v0[i] = key[i] ^ c0;
+    s.v1[i] = swap_halves(key[i]) ^ c1;
+    s.mul0[i] = c0;
+    s.mul1[i] = c1;
+  }
+}
+
+// ---------------------------------------------------------------- Section 4.1
+// ZipperMerge of one lane pair, added into dst.  With the pair's bytes
+// S0..S15 (lane a then lane b, little-endian) in 32-bit words w0..w3, result
+// byte i is S[P_i] for P = 3 12 2 5 14 1 15 0 | 11 4 10 13 9 6 8 7 (i = 0..15,
+// the printed map reversed).  Per result word:
+//   a.lo = w0.b3 w3.b0 w0.b2 w1.b1     a.hi = w3.b2 w0.b1 w3.b3 w0.b0
+//   b.lo = w2.b3 w1.b0 w2.b2 w3.b1     b.hi = w2.b1 w1.b2 w2.b0 w1.b3
+__device__ __forceinline__ void zipper_add_pair(uint64_t& dst_a, uint64_t& dst_b,
+                                                uint64_t a, uint64_t b) {
+  const uint32_t w0 = lo32(a), w1 = hi32(a), w2 = lo32(b), w3 = hi32(b);
+  const uint32_t a_lo = __byte_perm(__byte_perm(w0, w3, 0x0243), w1, 0x5210);
+  const uint32_t a_hi = __byte_perm(w0, w3, 0x0716);
+  const uint32_t b_lo = __byte_perm(__byte_perm(w2, w1, 0x0243), w3, 0x5210);
+  const uint32_t b_hi = __byte_perm(w2, w1, 0x7061);
+  dst_a += join(a_lo, a_hi);
+  dst_b += join(b_lo, b_hi);
+}
+
+// _mm256_mul_epu32 per lane: low 32 bits times low 32 bits, 64-bit product.
+__device__ __forceinline__ uint64_t mul_lo(uint64_t a, uint64_t b) {
+  return static_cast<uint64_t>(lo32(a)) * lo32(b);
+}
+
+// ---------------------------------------------------------------- Section 4.2
+__device__ __forceinline__ void update(State& s, const uint64_t p[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    s.v1[i] += p[i] + s.mul0[i];
+    s.mul0[i] ^= mul_lo(s.v1[i], s.v0[i] >> 32);
+    s.v0[i] += s.mul1[i];
+    s.mul1[i] ^= mul_lo(s.v0[i], s.v1[i] >> 32);
+  }
+  zipper_add_pair(s.v0[0], s.v0[1], s.v1[0], s.v1[1]);
+  zipper_add_pair(s.v0[2], s.v0[3], s.v1[2], s.v1[3]);
+  zipper_add_pair(s.v1[0], s.v1[1], s.v0[0], s.v0[1]);
+  zipper_add_pair(s.v1[2], s.v1[3], s.v0[2], s.v0[3]);
+}
+
+// Packet from eight little-endian 32-bit words.
+__device__ __forceinline__ void update_words(State& s, const uint32_t w[8]) {
+  const uint64_t p[4] = {join(w[0], w[1]), join(w[2], w[3]), join(w[4], w[5]), join(w[6], w[7])};
+  update(s, p);
+}
+
+// ---------------------------------------------------------------- Section 4.5
+// tail[0..7] hold the bytes that follow the last whole packet (only the first
+// r = size mod 32 bytes are meaningful; the rest may be anything).  For r != 0:
+// add (r << 32) + r to each lane of v0, rotate each 32-bit half of v1 left by
+// r, then Update with a packet that keeps the whole 4-byte groups of the tail
+// in place and puts the last r mod 4 bytes into bytes 28.. of the packet.
+__device__ __forceinline__ void remainder(State& s, uint32_t r, const uint32_t tail[8]) {
+  if (r == 0) return;
+  const uint64_t inject = (static_cast<uint64_t>(r) << 32) + r;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    s.v0[i] += inject;
+    const uint32_t lo = lo32(s.v1[i]), hi = hi32(s.v1[i]);
+    s.v1[i] = join(__funnelshift_l(lo, lo, r), __funnelshift_l(hi, hi, r));
+  }
+  const uint32_t whole = r >> 2, extra = r & 3;
+  uint32_t pkt[8];
+  uint32_t last = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    pkt[j] = (static_cast<uint32_t>(j) < whole) ? tail[j] : 0u;
+    last = (static_cast<uint32_t>(j) == whole) ? tail[j] : last;
+  }
+  if (extra) pkt[7] |= last & ((1u << (8 * extra)) - 1u);
+  update_words(s, pkt);
+}
+
+// ---------------------------------------------------------------- Section 4.3
+// Four rounds of Update(Permute(v0)); Permute swaps v0's 128-bit halves and
+// the 32-bit halves of every lane (index map 2 3 0 1 6 7 4 5).
+__device__ __forceinline__ void finalize(State& s) {
+#pragma unroll
+  for (int round = 0; round < 4; ++round) {
+    const uint64_t p[4] = {swap_halves(s.v0[2]), swap_halves(s.v0[3]), swap_halves(s.v0[0]),
+                           swap_halves(s.v0[1])};
+    update(s, p);
+  }
+}
+
+// h[i] = v0[i] + v1[i] + mul0[i] + mul1[i]; the 64-bit hash is h[0], the
+// 128-bit hash h[0..1], the 256-bit hash h[0..3].
+__device__ __forceinline__ void digest(const State& s, uint64_t h[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) h[i] = s.v0[i] + s.v1[i] + s.mul0[i] + s.mul1[i];
+}
+
+}  // namespace hh

@@ -1,0 +1,60 @@
+// hh_internal.h -- declarations shared by the translation units of libhh.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace hh {
+
+// Device error codes (same values as enum hh_status in include/hh.h).
+constexpr int kErrTimeout = 4;
+constexpr int kErrBadOffsets = 6;
+
+// Length-sort buckets: bucket = min(ceil(len / 32), kBuckets - 1), i.e. the
+// number of Updates a message needs before finalisation, capped.
+constexpr int kBuckets = 4096;
+
+// Messages per work tile of the staged kernel: one thread per message.
+constexpr int kTileRows = 128;
+
+// One batch, as every kernel sees it.
+struct Batch {
+  const uint8_t* bytes;      // message bytes
+  const int64_t* offsets;    // n + 1 offsets, or null for the fixed-length form
+  int64_t fixed_len;         // message length when offsets == null
+  const uint64_t* keys;      // 4 words (shared) or 4 * n words (per message)
+  int per_message_keys;
+  int64_t n;
+  uint64_t* out;             // words * n
+  int words;                 // 1, 2 or 4
+  int* err;                  // device error word (first error wins)
+};
+
+// Work-queue state of the staged kernel.
+struct Queue {
+  const int32_t* perm;       // processing order of messages, or null = 0..n-1
+  unsigned long long* next_tile;  // atomic tile counter (sorted order), or null = static
+  int64_t tiles;
+};
+
+// Staged-kernel shapes: bytes of each message staged per pipeline step (W)
+// and the number of pipeline buffers.
+struct StagedShape {
+  int window;   // 128 or 256
+  int stages;   // 2..4
+};
+
+// Launchers (return the CUDA error of the launch).
+cudaError_t launch_naive(const Batch& b, cudaStream_t stream);
+cudaError_t launch_staged(const Batch& b, const Queue& q, StagedShape shape, bool aligned16,
+                          int num_sms, cudaStream_t stream);
+int staged_blocks_per_sm(StagedShape shape, bool aligned16);
+size_t staged_smem_bytes(StagedShape shape);
+
+// Length bucketing: hist and cursor are kBuckets words; perm n words.
+cudaError_t launch_bucket_sort(const int64_t* offsets, int64_t n, uint32_t* hist,
+                               uint32_t* cursor, int32_t* perm, unsigned long long* next_tile,
+                               int num_sms, cudaStream_t stream, int* launches);
+
+}  // namespace hh

@@ -1,0 +1,49 @@
+"""A small, self-contained hash launch to run under a profiler.
+
+    python -m paper_1612_06257_gb300.profile_case --kind fixed --n 262144 --length 1024
+
+builds one seeded batch on cuda:0 and hashes it `--reps` times through the C
+ABI (the first launch warms up; profile with `-s 1 -c 1` to capture the
+second).  Kinds: fixed (hh_hash_fixed), ragged (log-uniform lengths,
+per-message keys) and short (0..64-byte messages).
+"""
+import argparse
+
+import torch
+
+from paper_1612_06257_gb300 import hh, workloads
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--kind", choices=["fixed", "ragged", "short"], default="fixed")
+    p.add_argument("--n", type=int, default=1 << 18)
+    p.add_argument("--length", type=int, default=1024)
+    p.add_argument("--bits", type=int, default=64)
+    p.add_argument("--reps", type=int, default=2)
+    p.add_argument("--kernel", type=int, default=hh.HH_KERNEL_AUTO)
+    a = p.parse_args()
+    ctx = hh.hh_init(0)
+    hh.hh_set_kernel(ctx, a.kernel)
+    dev = "cuda:0"
+    if a.kind == "fixed":
+        w = workloads.fixed(a.n, a.length, seed=1, device=dev)
+    elif a.kind == "ragged":
+        w = workloads.ragged(a.n, seed=1, device=dev)
+    else:
+        w = workloads.short(a.n, seed=1, device=dev)
+    out = torch.empty(w.n * a.bits // 64, dtype=torch.int64, device=dev)
+    for _ in range(a.reps):
+        if a.kind == "fixed":
+            hh.hh_hash_fixed(ctx, a.bits, w.keys, w.key_mode, w.data, a.length, w.n, out=out)
+        else:
+            fn = {64: hh.hh_hash64_batch, 128: hh.hh_hash128_batch, 256: hh.hh_hash256_batch}
+            fn[a.bits](ctx, w.keys, w.key_mode, w.data, w.offsets, out=out)
+    status = hh.hh_get_device_error(ctx)
+    if status != hh.HH_OK:
+        raise SystemExit("device error: " + hh.hh_status_string(status))
+    print("ok", a.kind, w.n, w.total_bytes)
+
+
+if __name__ == "__main__":
+    main()

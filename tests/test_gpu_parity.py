@@ -1,0 +1,263 @@
+"""GPU parity: libhh (through the C ABI) against the CPU oracle, bit for bit.
+
+HighwayHash is exact integer arithmetic, so the tolerance is zero: every
+output word must equal the oracle's.  Small cases are checked on every
+message; the full configuration sizes (the ones the benchmark times) are
+checked on seeded random samples of messages plus properties that hold at any
+size.  Parity with any released HighwayHash library is not claimed: the
+oracle implements the paper's definition.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1612_06257_gb300 import hh, workloads
+from tests.helpers import as_u64, oracle_hashes
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+WORDS = {64: 1, 128: 2, 256: 4}
+RAGGED_FN = {64: hh.hh_hash64_batch, 128: hh.hh_hash128_batch, 256: hh.hh_hash256_batch}
+KERNELS = {"auto": hh.HH_KERNEL_AUTO, "naive": hh.HH_KERNEL_NAIVE,
+           "unsorted": hh.HH_KERNEL_STAGED_UNSORTED}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1612_06257_gb300 import build
+    build.build()
+    c = hh.hh_init(0)
+    yield c
+    hh.hh_destroy(c)
+
+
+def run_ragged(ctx, w, bits, kernel="auto"):
+    hh.hh_set_kernel(ctx, KERNELS[kernel])
+    try:
+        out = RAGGED_FN[bits](ctx, w.keys, w.key_mode, w.data, w.offsets_or_stride())
+        assert hh.hh_get_device_error(ctx) == hh.HH_OK
+    finally:
+        hh.hh_set_kernel(ctx, hh.HH_KERNEL_AUTO)
+    return as_u64(out, WORDS[bits])
+
+
+def run_fixed(ctx, w, bits, kernel="auto"):
+    hh.hh_set_kernel(ctx, KERNELS[kernel])
+    try:
+        out = hh.hh_hash_fixed(ctx, bits, w.keys, w.key_mode, w.data, w.fixed_len, w.n)
+        assert hh.hh_get_device_error(ctx) == hh.HH_OK
+    finally:
+        hh.hh_set_kernel(ctx, hh.HH_KERNEL_AUTO)
+    return as_u64(out, WORDS[bits])
+
+
+# ------------------------------------------------------------ every message
+
+@pytest.mark.parametrize("bits", [64, 128, 256])
+def test_fixed_1k_messages_4096(ctx, bits):
+    """4096 messages of 1024 bytes, one key (the small fixed-length batch)."""
+    w = workloads.fixed(4096, 1024, seed=1, device=DEV)
+    expect = oracle_hashes(w, bits)
+    assert np.array_equal(run_fixed(ctx, w, bits), expect)
+    assert np.array_equal(run_fixed(ctx, w, bits, "naive"), expect)
+    assert np.array_equal(run_ragged(ctx, w, bits), expect)
+
+
+@pytest.mark.parametrize("length", [0, 1, 3, 16, 31, 32, 33, 48, 63, 64, 100, 1024, 1041, 4096])
+@pytest.mark.parametrize("per_message_keys", [False, True])
+def test_fixed_lengths(ctx, length, per_message_keys):
+    """Fixed lengths with and without 16-byte alignment; 300 messages = 2 full
+    tiles of 128 plus a ragged tail of 44."""
+    w = workloads.fixed(300, length, seed=2 + length, device=DEV,
+                        per_message_keys=per_message_keys)
+    for bits in (64, 256):
+        expect = oracle_hashes(w, bits)
+        assert np.array_equal(run_fixed(ctx, w, bits), expect), (length, bits)
+
+
+def test_fixed_unaligned_base_pointer(ctx):
+    """The byte buffer starts 3 bytes into an allocation: no 16-byte alignment."""
+    n, length = 257, 64
+    g = workloads.generator(3, DEV)
+    backing = workloads.random_bytes(n * length + 3, g, DEV)
+    w = workloads.Workload("fixed", backing[3:], None, length,
+                           workloads.random_u64((4,), g, DEV), False, n)
+    expect = oracle_hashes(w, 64)
+    assert np.array_equal(run_fixed(ctx, w, 64), expect)
+
+
+@pytest.mark.parametrize("kernel", ["auto", "unsorted", "naive"])
+def test_every_length_0_to_1024(ctx, kernel):
+    """Two messages of every length 0..1024 in shuffled order (every residue
+    mod 32 many times, every byte alignment), per-message keys, all widths."""
+    lengths = torch.arange(0, 1025).repeat(2)
+    lengths = lengths[torch.randperm(lengths.numel(), generator=torch.Generator().manual_seed(5))]
+    w = workloads.from_lengths(lengths, seed=5, device=DEV, per_message_keys=True)
+    for bits in (64, 128, 256):
+        assert np.array_equal(run_ragged(ctx, w, bits, kernel), oracle_hashes(w, bits)), bits
+
+
+def test_ragged_loguniform_small(ctx):
+    """The log-uniform ragged recipe (lengths 0..65536, per-message keys) at
+    n = 16384; all messages checked."""
+    w = workloads.ragged(16384, seed=6, device=DEV)
+    expect = oracle_hashes(w, 64)
+    assert np.array_equal(run_ragged(ctx, w, 64), expect)
+    assert np.array_equal(run_ragged(ctx, w, 64, "unsorted"), expect)
+
+
+@pytest.mark.parametrize("bits", [64, 128])
+def test_short_messages_small(ctx, bits):
+    """Lengths uniform in [0, 64], 10% all-zero messages, one key; n = 65536."""
+    w = workloads.short(65536, seed=7, device=DEV)
+    assert np.array_equal(run_ragged(ctx, w, bits), oracle_hashes(w, bits))
+
+
+def test_kernels_agree_on_mixed_batch(ctx):
+    lengths = torch.cat([torch.randint(0, 65, (3000,)), torch.full((200,), 1024),
+                         torch.randint(1 << 15, 1 << 17, (20,))])
+    w = workloads.from_lengths(lengths, seed=8, device=DEV, per_message_keys=True)
+    results = [run_ragged(ctx, w, 256, k) for k in ("auto", "unsorted", "naive")]
+    assert np.array_equal(results[0], results[1]) and np.array_equal(results[0], results[2])
+    assert np.array_equal(results[0], oracle_hashes(w, 256))
+
+
+# ----------------------------------------------------------------- edge cases
+
+def test_empty_batch_is_a_noop(ctx):
+    keys = torch.zeros(4, dtype=torch.int64, device=DEV)
+    data = torch.zeros(16, dtype=torch.uint8, device=DEV)
+    offsets = torch.zeros(1, dtype=torch.int64, device=DEV)
+    out = torch.full((4,), 7, dtype=torch.int64, device=DEV)
+    hh.hh_hash64_batch(ctx, keys, 0, data, offsets, n=0, out=out)
+    assert hh.hh_last_launch_count(ctx) == 0
+    assert out.tolist() == [7, 7, 7, 7]
+
+
+def test_all_empty_messages(ctx):
+    w = workloads.from_lengths([0] * 2000, seed=9, device=DEV, per_message_keys=True)
+    w.data = torch.zeros(16, dtype=torch.uint8, device=DEV)  # unused, must be non-null
+    assert np.array_equal(run_ragged(ctx, w, 128), oracle_hashes(w, 128))
+
+
+def test_offsets_not_starting_at_zero_and_exact_end(ctx):
+    """Messages occupy bytes [100, total) of the buffer, the last one ending on
+    the buffer's last byte, and the buffer length is not a multiple of 16."""
+    lengths = torch.tensor([5, 33, 0, 64, 1, 100, 31, 17])
+    w = workloads.from_lengths(lengths, seed=10, device=DEV)
+    pad = torch.zeros(100, dtype=torch.uint8, device=DEV)
+    data = torch.cat([pad, w.data])
+    assert data.numel() % 16 != 0
+    shifted = workloads.Workload("shifted", data, w.offsets + 100, None, w.keys, True, w.n)
+    expect = oracle_hashes(w, 64)
+    for kernel in ("auto", "naive", "unsorted"):
+        assert np.array_equal(run_ragged(ctx, shifted, 64, kernel), expect)
+
+
+def test_output_guard_words_untouched(ctx):
+    w = workloads.ragged(3000, seed=11, device=DEV, max_len=3000)
+    out = torch.full((3000 * 2 + 64,), -0x5A5A5A5A5A5A5A5B, dtype=torch.int64, device=DEV)
+    hh.hh_hash128_batch(ctx, w.keys, w.key_mode, w.data, w.offsets, out=out)
+    assert hh.hh_get_device_error(ctx) == hh.HH_OK
+    assert torch.all(out[6000:] == -0x5A5A5A5A5A5A5A5B)
+    assert np.array_equal(as_u64(out[:6000], 2), oracle_hashes(w, 128))
+
+
+def test_decreasing_offsets_set_device_error(ctx):
+    lengths = torch.tensor([10, 20, 30, 40])
+    w = workloads.from_lengths(lengths, seed=12, device=DEV)
+    bad = w.offsets.clone()
+    bad[2] = bad[1] - 5  # message 1 has end < start; message 2 is long but valid
+    out = hh.hh_hash64_batch(ctx, w.keys, 1, w.data, bad)
+    assert hh.hh_get_device_error(ctx) == hh.HH_ERR_BAD_OFFSETS
+    assert int(out[1].item()) == 0
+    assert hh.hh_get_device_error(ctx) == hh.HH_OK  # cleared by the read
+
+
+def test_invalid_arguments(ctx):
+    keys = torch.zeros(4, dtype=torch.int64, device=DEV)
+    data = torch.zeros(64, dtype=torch.uint8, device=DEV)
+    offsets = torch.tensor([0, 64], dtype=torch.int64, device=DEV)
+    L = hh.load_library()
+    stream = torch.cuda.current_stream().cuda_stream
+    out = torch.zeros(4, dtype=torch.int64, device=DEV)
+    assert L.hh_hash64_batch(ctx.ptr, keys.data_ptr(), 2, data.data_ptr(), offsets.data_ptr(), 1,
+                             out.data_ptr(), stream) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_hash64_batch(ctx.ptr, keys.data_ptr(), 0, data.data_ptr(), None, 1,
+                             out.data_ptr(), stream) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_hash64_batch(ctx.ptr, keys.data_ptr(), 0, data.data_ptr(), offsets.data_ptr(), -1,
+                             out.data_ptr(), stream) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_hash_fixed(ctx.ptr, 96, keys.data_ptr(), 0, data.data_ptr(), 64, 1,
+                           out.data_ptr(), stream) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_set_kernel(ctx.ptr, 17) == hh.HH_ERR_INVALID_ARG
+
+
+def test_determinism_and_widths_share_lanes(ctx):
+    w = workloads.ragged(5000, seed=13, device=DEV, max_len=4096)
+    h64 = run_ragged(ctx, w, 64)
+    h128 = run_ragged(ctx, w, 128)
+    h256 = run_ragged(ctx, w, 256)
+    assert np.array_equal(h64[:, 0], h256[:, 0]) and np.array_equal(h128, h256[:, :2])
+    assert np.array_equal(run_ragged(ctx, w, 256), h256)
+
+
+def test_host_buffer_entry_point(ctx):
+    """hh_hash_host with pinned host buffers, several chunks, per-message keys."""
+    w = workloads.ragged(40000, seed=14, device=DEV, max_len=8192)
+    assert w.total_bytes > (64 << 20) // 2
+    keys = w.keys.cpu().numpy().view(np.uint64).copy()
+    data = w.data.cpu().pin_memory().numpy()
+    offsets = w.offsets.cpu().numpy()
+    out = hh.hh_hash_host(ctx, 128, keys.reshape(-1), 1, data, offsets)
+    assert np.array_equal(out.reshape(-1, 2), oracle_hashes(w, 128))
+    big = workloads.fixed(1 << 17, 1024, seed=15, device=DEV)  # 128 MiB: 2+ chunks
+    offs = big.offsets_or_stride().cpu().numpy()
+    out = hh.hh_hash_host(ctx, 64, big.keys.cpu().numpy().view(np.uint64).copy(), 0,
+                          big.data.cpu().numpy(), offs)
+    sample = np.random.default_rng(15).choice(big.n, 500, replace=False)
+    assert np.array_equal(out[sample], oracle_hashes(big, 64, indices=sample)[:, 0])
+
+
+# ------------------------------------------- full configuration sizes, sampled
+
+def _sample(n, count, seed):
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(n, size=min(count, n), replace=False)
+    return np.sort(np.concatenate([idx, [0, n - 1]]).astype(np.int64))
+
+
+@pytest.mark.parametrize("bits", [64, 128, 256])
+def test_full_size_1gib_fixed_1k(ctx, bits):
+    """2^20 messages of 1024 bytes (1 GiB), one key: the benchmark's launch."""
+    w = workloads.fixed(1 << 20, 1024, seed=21, device=DEV)
+    got = run_fixed(ctx, w, bits)
+    idx = _sample(w.n, 3000, 21)
+    assert np.array_equal(got[idx], oracle_hashes(w, bits, indices=idx))
+    # Distinct random messages give distinct 64-bit hashes (a collision among
+    # 2^20 would have probability about 2^-25).
+    assert np.unique(got[:, 0]).size == w.n
+
+
+def test_full_size_ragged_4m_messages(ctx):
+    """2^22 log-uniform messages (about 25 GB) with per-message keys."""
+    w = workloads.ragged(1 << 22, seed=22, device=DEV)
+    got = run_ragged(ctx, w, 64)
+    lengths = (w.offsets[1:] - w.offsets[:-1]).cpu().numpy()
+    idx = _sample(w.n, 2000, 22)
+    longest = np.argsort(lengths)[-50:]
+    idx = np.unique(np.concatenate([idx, longest]))
+    assert np.array_equal(got[idx], oracle_hashes(w, 64, indices=idx))
+    del w
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("bits", [64, 128])
+def test_full_size_short_64m_messages(ctx, bits):
+    """2^26 messages of 0..64 bytes, 10% all zero, one key."""
+    w = workloads.short(1 << 26, seed=23, device=DEV)
+    got = run_ragged(ctx, w, bits)
+    idx = _sample(w.n, 20000, 23)
+    assert np.array_equal(got[idx], oracle_hashes(w, bits, indices=idx))
+    del w
+    torch.cuda.empty_cache()
