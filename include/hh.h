@@ -153,17 +153,31 @@ int hh_get_device_error(hh_ctx* ctx, void* stream);
 /* Force one kernel family (enum hh_kernel) for later calls on ctx. */
 int hh_set_kernel(hh_ctx* ctx, int kernel);
 
-/* Batch regimes that have their own staged-kernel shape. */
+/* Batch regimes that have their own kernel shape. */
 enum hh_regime {
-  HH_REGIME_FIXED = 0,      /* hh_hash_fixed                                  */
+  HH_REGIME_FIXED = 0,      /* hh_hash_fixed on 16-byte aligned lengths (TMA) */
   HH_REGIME_RAGGED = 1      /* the offsets-based calls                        */
 };
 
-/* Set the staged kernel's shape for one regime: `window` bytes of every
- * message staged per pipeline step and `stages` pipeline buffers.  Supported
- * (window, stages): (128, 3), (128, 4), (256, 2), (256, 3).  Other pairs
- * return HH_ERR_INVALID_ARG. */
+/* Set a kernel shape for one regime: `window` bytes of every message staged
+ * per pipeline step and `stages` pipeline buffers.  Supported (window,
+ * stages): HH_REGIME_FIXED (128, 4), (128, 6), (256, 3); HH_REGIME_RAGGED
+ * (128, 3), (128, 4), (256, 2), (256, 3).  Other pairs return
+ * HH_ERR_INVALID_ARG. */
 int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages);
+
+/*
+ * Integer-issue microbenchmark (no counterpart in the paper; it measures the
+ * ceiling the integer pipes put on Section 4.2's Update).  Each of `threads`
+ * threads (a multiple of 256) runs `updates` Updates on register state with
+ * no memory traffic and writes one word to out[thread] (device uint64
+ * [threads]).  `variant` 0..HH_UPDATE_VARIANTS-1 selects how the 64-bit adds
+ * are split between the ALU and FMA pipes; every variant gives identical
+ * output words.
+ */
+#define HH_UPDATE_VARIANTS 5
+int hh_update_microbench(hh_ctx* ctx, int variant, int64_t updates, int64_t threads,
+                         uint64_t* out, void* stream);
 
 /* Number of kernel launches the last hash call on ctx enqueued. */
 int hh_last_launch_count(hh_ctx* ctx);

@@ -59,8 +59,8 @@ struct hh_ctx {
   uint32_t* d_cursor = nullptr;
   int32_t* d_perm = nullptr;
   int64_t perm_cap = 0;
-  hh::StagedShape shape_ragged{128, 3};
-  hh::StagedShape shape_fixed{128, 3};
+  hh::StagedShape shape_ragged{256, 2};
+  hh::StagedShape shape_fixed{128, 4};   // the TMA kernel's shape
   int last_launches = 0;
   // Host-buffer path.
   cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
@@ -130,13 +130,17 @@ int hash_device(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode, const
     return to_status(hh::launch_naive(b, stream));
   }
 
+  if (offsets == nullptr && hh::fixed_tma_supported(bytes, fixed_len, n)) {
+    ctx->last_launches = 1;
+    return to_status(hh::launch_fixed_tma(b, ctx->shape_fixed, ctx->num_sms, stream));
+  }
+
   hh::Queue q{};
   q.tiles = (n + hh::kTileRows - 1) / hh::kTileRows;
   bool aligned16 = false;
   hh::StagedShape shape = ctx->shape_ragged;
   if (offsets == nullptr) {
     aligned16 = (reinterpret_cast<uintptr_t>(bytes) % 16 == 0) && (fixed_len % 16 == 0);
-    shape = ctx->shape_fixed;
   } else if (ctx->kernel != HH_KERNEL_STAGED_UNSORTED && n >= kSortMinMessages) {
     if (n > kMaxSortedMessages) return HH_ERR_TOO_LARGE;
     int st = ensure_perm(ctx, n, stream);
@@ -400,13 +404,29 @@ int hh_set_kernel(hh_ctx* ctx, int kernel) {
 
 int hh_last_launch_count(hh_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
 
+int hh_update_microbench(hh_ctx* ctx, int variant, int64_t updates, int64_t threads,
+                         uint64_t* out, void* stream) {
+  if (ctx == nullptr || out == nullptr || updates < 0 || threads <= 0 || threads % 256 != 0 ||
+      threads / 256 > INT32_MAX || variant < 0 || variant >= HH_UPDATE_VARIANTS)
+    return HH_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return HH_ERR_CUDA;
+  ctx->last_launches = 1;
+  return to_status(hh::launch_update_microbench(variant, updates, threads, out,
+                                                static_cast<cudaStream_t>(stream)));
+}
+
 int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages) {
   if (ctx == nullptr || (regime != HH_REGIME_FIXED && regime != HH_REGIME_RAGGED))
     return HH_ERR_INVALID_ARG;
   const hh::StagedShape shape{window, stages};
-  if (hh::staged_smem_bytes(shape) == 0) return HH_ERR_INVALID_ARG;
-  if (regime == HH_REGIME_FIXED) ctx->shape_fixed = shape;
-  else ctx->shape_ragged = shape;
+  if (regime == HH_REGIME_FIXED) {
+    if (!hh::fixed_shape_valid(shape)) return HH_ERR_INVALID_ARG;
+    ctx->shape_fixed = shape;
+  } else {
+    if (hh::staged_smem_bytes(shape) == 0) return HH_ERR_INVALID_ARG;
+    ctx->shape_ragged = shape;
+  }
   return HH_OK;
 }
 

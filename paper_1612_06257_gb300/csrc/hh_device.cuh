@@ -85,24 +85,96 @@ __device__ __forceinline__ uint64_t mul_lo(uint64_t a, uint64_t b) {
 }
 
 // ---------------------------------------------------------------- Section 4.2
-__device__ __forceinline__ void update(State& s, const uint64_t p[4]) {
+// x + y with both halves on the multiply-add (FMA) pipe:
+//   t = lo(y) * one + x (64-bit mad.wide), then hi(t) += hi(y) * one.
+// `one` is always 1 but arrives at run time, so the compiler cannot turn
+// these back into IADD3; moving adds to the FMA pipe relieves the ALU pipe,
+// which runs the PRMT, LOP3 and remaining IADD3 of Update.
+__device__ __forceinline__ uint64_t add_on_fma(uint64_t x, uint64_t y, uint32_t one) {
+  uint64_t t;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(t) : "r"(lo32(y)), "r"(one), "l"(x));
+  uint32_t hi;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(hi) : "r"(hi32(y)), "r"(one), "r"(hi32(t)));
+  return join(lo32(t), hi);
+}
+
+// ZipperMerge of a lane pair as two words (no add).
+__device__ __forceinline__ void zipper_pair(uint64_t a, uint64_t b, uint64_t& za, uint64_t& zb) {
+  const uint32_t w0 = lo32(a), w1 = hi32(a), w2 = lo32(b), w3 = hi32(b);
+  za = join(__byte_perm(__byte_perm(w0, w3, 0x0243), w1, 0x5210), __byte_perm(w0, w3, 0x0716));
+  zb = join(__byte_perm(__byte_perm(w2, w1, 0x0243), w3, 0x5210), __byte_perm(w2, w1, 0x7061));
+}
+
+// Update variants: the same arithmetic, with the 64-bit additions split
+// differently between the ALU and FMA pipes (see the microbenchmark).
+//   0: plain C, the compiler's choice.
+//   1: v0 + mul1 + ZM(v1) as one 3-input add; only lo(v0 + mul1) is formed
+//      separately for the multiply.
+//   2: as 1, and v1 += ZM(v0) on the FMA pipe.
+//   3: v0 += mul1 on the ALU, v0 += ZM(v1) and v1 += ZM(v0) on the FMA pipe.
+//   4: as 3, and v1 += packet + mul0 on the FMA pipe as well.
+template <int V>
+__device__ __forceinline__ void update_v(State& s, const uint64_t p[4], uint32_t one) {
+  if (V == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      s.v1[i] += p[i] + s.mul0[i];
+      s.mul0[i] ^= mul_lo(s.v1[i], s.v0[i] >> 32);
+      s.v0[i] += s.mul1[i];
+      s.mul1[i] ^= mul_lo(s.v0[i], s.v1[i] >> 32);
+    }
+    zipper_add_pair(s.v0[0], s.v0[1], s.v1[0], s.v1[1]);
+    zipper_add_pair(s.v0[2], s.v0[3], s.v1[2], s.v1[3]);
+    zipper_add_pair(s.v1[0], s.v1[1], s.v0[0], s.v0[1]);
+    zipper_add_pair(s.v1[2], s.v1[3], s.v0[2], s.v0[3]);
+    return;
+  }
+  // V 1-2: add[i] = mul1 before its update (v0 + add + ZM(v1) is one 3-input
+  // add later).  V 3-4: add[i] = v0 + mul1, formed now.
+  uint64_t add[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    s.v1[i] += p[i] + s.mul0[i];
+    if (V == 4) s.v1[i] = add_on_fma(add_on_fma(s.v1[i], p[i], one), s.mul0[i], one);
+    else s.v1[i] += p[i] + s.mul0[i];
     s.mul0[i] ^= mul_lo(s.v1[i], s.v0[i] >> 32);
-    s.v0[i] += s.mul1[i];
-    s.mul1[i] ^= mul_lo(s.v0[i], s.v1[i] >> 32);
+    if (V >= 3) {
+      add[i] = s.v0[i] + s.mul1[i];
+      s.mul1[i] ^= mul_lo(add[i], s.v1[i] >> 32);
+    } else {
+      add[i] = s.mul1[i];
+      const uint32_t lo = lo32(s.v0[i]) + lo32(add[i]);  // lo(v0 + mul1)
+      s.mul1[i] ^= static_cast<uint64_t>(lo) * hi32(s.v1[i]);
+    }
   }
-  zipper_add_pair(s.v0[0], s.v0[1], s.v1[0], s.v1[1]);
-  zipper_add_pair(s.v0[2], s.v0[3], s.v1[2], s.v1[3]);
-  zipper_add_pair(s.v1[0], s.v1[1], s.v0[0], s.v0[1]);
-  zipper_add_pair(s.v1[2], s.v1[3], s.v0[2], s.v0[3]);
+  uint64_t z[4];
+  zipper_pair(s.v1[0], s.v1[1], z[0], z[1]);
+  zipper_pair(s.v1[2], s.v1[3], z[2], z[3]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    s.v0[i] = (V >= 3) ? add_on_fma(add[i], z[i], one) : s.v0[i] + add[i] + z[i];
+  zipper_pair(s.v0[0], s.v0[1], z[0], z[1]);
+  zipper_pair(s.v0[2], s.v0[3], z[2], z[3]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) s.v1[i] = (V >= 2) ? add_on_fma(s.v1[i], z[i], one) : s.v1[i] + z[i];
+}
+
+// The variant every kernel uses: fastest in the Update-rate microbenchmark on
+// GB300 (all ALU; moving adds to IMAD.WIDE was slower).
+constexpr int kFastUpdate = 1;
+
+__device__ __forceinline__ void update(State& s, const uint64_t p[4]) {
+  update_v<kFastUpdate>(s, p, 1u);
 }
 
 // Packet from eight little-endian 32-bit words.
-__device__ __forceinline__ void update_words(State& s, const uint32_t w[8]) {
+template <int V>
+__device__ __forceinline__ void update_words_v(State& s, const uint32_t w[8], uint32_t one) {
   const uint64_t p[4] = {join(w[0], w[1]), join(w[2], w[3]), join(w[4], w[5]), join(w[6], w[7])};
-  update(s, p);
+  update_v<V>(s, p, one);
+}
+
+__device__ __forceinline__ void update_words(State& s, const uint32_t w[8]) {
+  update_words_v<kFastUpdate>(s, w, 1u);
 }
 
 // ---------------------------------------------------------------- Section 4.5

@@ -1,0 +1,252 @@
+// hh_fixed.cu -- fixed-length batches through 2D tensor-map TMA loads.
+//
+// A batch of n messages of `len` bytes (len a multiple of 16, 16-byte aligned
+// base) is a 2D byte tensor [n][len].  A CTA of 128 threads owns tiles of 128
+// consecutive messages (one thread per message, the 1024-bit state in
+// registers).  For each W-byte window of the tile one thread issues W/128
+// tensor loads of a 128-row x 128-byte box (128-byte swizzle) into a shared
+// memory stage; NST stages form a ring guarded by "full" mbarriers (TMA
+// transaction bytes) and "empty" mbarriers (one arrival per warp once it has
+// read the stage).  The stream of (tile, window) pairs runs on across tiles,
+// so the next tile's first windows load while the current one finishes.
+//
+// Thread t reads its 32-byte packets from row t of the box: 16-byte chunk c
+// lies at chunk position c ^ (t & 7), so the 8 threads of a quarter-warp hit
+// 8 distinct chunks (all 32 banks) on every 128-bit shared load.  Bytes past
+// the end of a message and rows past the end of the batch are zero-filled by
+// the TMA unit; they are never hashed.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hh_device.cuh"
+#include "hh_internal.h"
+#include "hh_ptx.cuh"
+
+namespace hh {
+namespace {
+
+constexpr int kRows = 128;           // messages per tile = box height = threads
+constexpr int kBoxBytes = 128 * kRows;
+
+struct FixedParams {
+  int64_t n;
+  int64_t len;
+  const uint64_t* keys;
+  int per_message_keys;
+  uint64_t* out;
+  int words;
+  int* err;
+  uint32_t one;
+};
+
+template <int W, int NST>
+struct FixedLayout {
+  static constexpr int kStageBytes = W * kRows;
+  static constexpr int kBarOffset = NST * kStageBytes;
+  static constexpr int kBytes = kBarOffset + 2 * NST * 8 + 1024;  // + alignment slack
+};
+
+__device__ __forceinline__ void load_swizzled_packet(const uint8_t* box, int row, int chunk,
+                                                     uint32_t w[8]) {
+  const uint8_t* r = box + row * 128;
+  const uint4 a = *reinterpret_cast<const uint4*>(r + (((chunk) ^ (row & 7)) << 4));
+  const uint4 b = *reinterpret_cast<const uint4*>(r + (((chunk + 1) ^ (row & 7)) << 4));
+  w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+  w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+}
+
+template <int W, int NST>
+__global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                          FixedParams p) {
+  using L = FixedLayout<W, NST>;
+  constexpr int kBoxes = W / 128;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kBarOffset);
+  uint64_t* empty = full + NST;
+
+  const int t = threadIdx.x, lane = t & 31;
+  const int64_t steps = (p.len + W - 1) / W;                 // windows per message (>= 1)
+  const int64_t tiles = (p.n + kRows - 1) / kRows;
+  const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t total = my_tiles * steps;                    // this CTA's (tile, window) stream
+
+  if (t == 0) {
+    prefetch_tensormap(&tmap);
+    for (int i = 0; i < NST; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kRows / 32);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int64_t g) {
+    const int b = static_cast<int>(g % NST);
+    const int64_t tile = blockIdx.x + (g / steps) * gridDim.x;
+    const int32_t x0 = static_cast<int32_t>((g % steps) * W);
+    mbar_arrive_expect_tx(&full[b], L::kStageBytes);
+#pragma unroll
+    for (int x = 0; x < kBoxes; ++x)
+      tma_load_2d(smem + b * L::kStageBytes + x * kBoxBytes, &tmap, x0 + 128 * x,
+                  static_cast<int32_t>(tile * kRows), &full[b]);
+  };
+  if (t == 0)
+    for (int64_t g = 0; g < NST && g < total; ++g) issue(g);
+
+  const int64_t packets = p.len >> 5;
+  const uint32_t r = static_cast<uint32_t>(p.len & 31);
+  const int64_t rem_step = r ? (packets * 32) / W : -1;
+  const int rem_off = r ? static_cast<int>(packets * 32 - rem_step * W) : 0;
+  uint64_t key[4];
+  if (!p.per_message_keys) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) key[i] = __ldg(p.keys + i);
+  }
+  State s;
+  int64_t m = 0;
+  bool ok = true;
+  for (int64_t g = 0; g < total; ++g) {
+    const int64_t k = g % steps;
+    if (k == 0) {
+      m = (blockIdx.x + (g / steps) * gridDim.x) * kRows + t;
+      if (p.per_message_keys) {
+        const uint64_t* kp = p.keys + 4 * (m < p.n ? m : 0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
+      }
+      init(s, key);
+    }
+    const int b = static_cast<int>(g % NST);
+    const uint32_t parity = static_cast<uint32_t>((g / NST) & 1);
+    if (ok && !mbar_wait_bounded(&full[b], parity, kWaitLimitNs)) {
+      ok = false;
+      record_error(p.err, kErrTimeout);
+    }
+    const uint8_t* stage = smem + b * L::kStageBytes;
+    if (ok) {
+      const int64_t p0 = k * (W / 32);
+#pragma unroll
+      for (int j = 0; j < W / 32; ++j) {
+        if (p0 + j < packets) {
+          uint32_t w[8];
+          load_swizzled_packet(stage + (j / 4) * kBoxBytes, t, (j % 4) * 2, w);
+          update_words_v<kFastUpdate>(s, w, p.one);
+        }
+      }
+      if (k == rem_step) {
+        uint32_t w[8];
+        load_swizzled_packet(stage + (rem_off / 128) * kBoxBytes, t, (rem_off % 128) / 16, w);
+        remainder(s, r, w);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[b]);
+    if (t == 0 && g + NST < total) {
+      if (!mbar_wait_bounded(&empty[b], parity, kWaitLimitNs)) {
+        record_error(p.err, kErrTimeout);
+      } else {
+        fence_proxy_async_smem();
+        issue(g + NST);
+      }
+    }
+    if (k == steps - 1 && m < p.n) {
+      finalize(s);
+      uint64_t h[4];
+      digest(s, h);
+      if (!ok) h[0] = h[1] = h[2] = h[3] = 0;
+      uint64_t* o = p.out + m * p.words;
+      o[0] = h[0];
+      if (p.words >= 2) o[1] = h[1];
+      if (p.words == 4) {
+        o[2] = h[2];
+        o[3] = h[3];
+      }
+    }
+  }
+  // Loads issued but never waited for (only after a timeout) get a bounded
+  // time to land before the CTA exits.
+  if (!ok && t == 0) {
+    for (int i = 0; i < NST; ++i) mbar_wait_bounded(&full[i], 0, kDrainLimitNs);
+  }
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  return fn;
+}
+
+template <int W, int NST>
+cudaError_t launch_fixed_t(const CUtensorMap& tmap, const FixedParams& p, int num_sms,
+                           cudaStream_t stream) {
+  using L = FixedLayout<W, NST>;
+  auto kern = fixed_tma_kernel<W, NST>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRows, L::kBytes);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t tiles = (p.n + kRows - 1) / kRows;
+  const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
+  const int grid = static_cast<int>(tiles < cap ? tiles : cap);
+  kern<<<grid, kRows, L::kBytes, stream>>>(tmap, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fixed_tma_supported(const uint8_t* bytes, int64_t len, int64_t n) {
+  return encode_fn() != nullptr && len > 0 && len % 16 == 0 &&
+         (reinterpret_cast<uintptr_t>(bytes) % 16) == 0 && n > 0 && n < (int64_t(1) << 31) &&
+         len < (int64_t(1) << 31);
+}
+
+bool fixed_shape_valid(StagedShape shape) {
+#define HH_VALID(W_, N_) \
+  if (shape.window == W_ && shape.stages == N_) return true;
+  HH_FIXED_SHAPES(HH_VALID)
+#undef HH_VALID
+  return false;
+}
+
+cudaError_t launch_fixed_tma(const Batch& b, StagedShape shape, int num_sms,
+                             cudaStream_t stream) {
+  EncodeTiledFn enc = encode_fn();
+  if (enc == nullptr) return cudaErrorNotSupported;
+  CUtensorMap tmap;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(b.fixed_len), static_cast<cuuint64_t>(b.n)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(b.fixed_len)};
+  const cuuint32_t box[2] = {128, kRows};
+  const cuuint32_t elem[2] = {1, 1};
+  CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(b.bytes), dims,
+                   strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  FixedParams p{b.n, b.fixed_len, b.keys, b.per_message_keys, b.out, b.words, b.err, 1u};
+#define HH_FIXED(W_, N_) \
+  if (shape.window == W_ && shape.stages == N_) return launch_fixed_t<W_, N_>(tmap, p, num_sms, stream);
+  HH_FIXED_SHAPES(HH_FIXED)
+#undef HH_FIXED
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace hh

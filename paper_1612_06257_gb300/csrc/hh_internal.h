@@ -52,6 +52,17 @@ cudaError_t launch_staged(const Batch& b, const Queue& q, StagedShape shape, boo
 int staged_blocks_per_sm(StagedShape shape, bool aligned16);
 size_t staged_smem_bytes(StagedShape shape);
 
+// Fixed-length batches through 2D tensor-map TMA (len % 16 == 0, 16-byte
+// aligned bytes).  Supported (window, stages) pairs:
+#define HH_FIXED_SHAPES(X) X(128, 4) X(128, 6) X(256, 3)
+bool fixed_tma_supported(const uint8_t* bytes, int64_t len, int64_t n);
+cudaError_t launch_fixed_tma(const Batch& b, StagedShape shape, int num_sms, cudaStream_t stream);
+bool fixed_shape_valid(StagedShape shape);
+
+// Update-rate microbenchmark (threads must be a multiple of 256).
+cudaError_t launch_update_microbench(int variant, int64_t updates, int64_t threads,
+                                     uint64_t* out, cudaStream_t stream);
+
 // Length bucketing: hist and cursor are kBuckets words; perm n words.
 cudaError_t launch_bucket_sort(const int64_t* offsets, int64_t n, uint32_t* hist,
                                uint32_t* cursor, int32_t* perm, unsigned long long* next_tile,

@@ -47,6 +47,7 @@ EXPORTS = (
     "hh_init", "hh_destroy", "hh_reserve", "hh_hash64_batch", "hh_hash128_batch",
     "hh_hash256_batch", "hh_hash_fixed", "hh_hash_host", "hh_get_device_error",
     "hh_set_kernel", "hh_last_launch_count", "hh_status_string", "hh_set_staged_shape",
+    "hh_update_microbench",
 )
 
 HH_REGIME_FIXED = 0
@@ -92,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.hh_set_kernel.argtypes = [_vp, _int]
         L.hh_last_launch_count.argtypes = [_vp]
         L.hh_set_staged_shape.argtypes = [_vp, _int, _int, _int]
+        L.hh_update_microbench.argtypes = [_vp, _int, _i64, _i64, _vp, _vp]
         L.hh_status_string.argtypes = [_int]
         L.hh_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -239,6 +241,17 @@ def hh_set_kernel(ctx, kernel: int) -> None:
 def hh_set_staged_shape(ctx, regime: int, window: int, stages: int) -> None:
     _check(load_library().hh_set_staged_shape(ctx.ptr, int(regime), int(window), int(stages)),
            "hh_set_staged_shape")
+
+
+def hh_update_microbench(ctx, variant: int, updates: int, threads: int, out=None, stream=None):
+    """Run the Update-rate microbenchmark; returns out (int64 [threads])."""
+    if out is None:
+        out = torch.empty(int(threads), dtype=torch.int64, device="cuda:%d" % ctx.device)
+    st = load_library().hh_update_microbench(ctx.ptr, int(variant), int(updates), int(threads),
+                                             _dev_ptr(out, "out", (torch.int64,), ctx.device),
+                                             _stream_ptr(stream, ctx.device))
+    _check(st, "hh_update_microbench")
+    return out
 
 
 def hh_last_launch_count(ctx) -> int:
