@@ -73,8 +73,9 @@ enum hh_key_mode {
 enum hh_kernel {
   HH_KERNEL_AUTO = 0,
   HH_KERNEL_NAIVE = 1,      /* one thread per message, direct global loads    */
-  HH_KERNEL_STAGED = 2,     /* length-sorted, shared-memory staged (bulk copy) */
-  HH_KERNEL_STAGED_UNSORTED = 3 /* staged, messages taken in index order      */
+  HH_KERNEL_STAGED = 2,     /* length-sorted warp tiles, cp.async staging     */
+  HH_KERNEL_STAGED_UNSORTED = 3, /* the same, messages in index order         */
+  HH_KERNEL_STAGED_BULK = 4 /* CTA tiles, one bulk async copy per thread      */
 };
 
 /*
@@ -156,12 +157,14 @@ int hh_set_kernel(hh_ctx* ctx, int kernel);
 /* Batch regimes that have their own kernel shape. */
 enum hh_regime {
   HH_REGIME_FIXED = 0,      /* hh_hash_fixed on 16-byte aligned lengths (TMA) */
-  HH_REGIME_RAGGED = 1      /* the offsets-based calls                        */
+  HH_REGIME_RAGGED = 1,     /* offsets-based calls (warp-tile kernel)         */
+  HH_REGIME_BULK = 2        /* HH_KERNEL_STAGED_BULK                          */
 };
 
 /* Set a kernel shape for one regime: `window` bytes of every message staged
  * per pipeline step and `stages` pipeline buffers.  Supported (window,
- * stages): HH_REGIME_FIXED (128, 4), (128, 6), (256, 3); HH_REGIME_RAGGED
+ * stages): HH_REGIME_FIXED (128, 2..4), (128, 6), (256, 2), (256, 3);
+ * HH_REGIME_RAGGED (128, 2..4), (256, 2), (256, 3); HH_REGIME_BULK
  * (128, 3), (128, 4), (256, 2), (256, 3).  Other pairs return
  * HH_ERR_INVALID_ARG. */
 int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages);

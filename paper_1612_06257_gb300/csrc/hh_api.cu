@@ -55,12 +55,14 @@ struct hh_ctx {
   int kernel = HH_KERNEL_AUTO;
   int* d_err = nullptr;
   unsigned long long* d_next_tile = nullptr;
+  int* d_use_perm = nullptr;
   uint32_t* d_hist = nullptr;
   uint32_t* d_cursor = nullptr;
   int32_t* d_perm = nullptr;
   int64_t perm_cap = 0;
-  hh::StagedShape shape_ragged{256, 2};
-  hh::StagedShape shape_fixed{128, 4};   // the TMA kernel's shape
+  hh::StagedShape shape_ragged{256, 2};  // warp-tile kernel
+  hh::StagedShape shape_fixed{128, 3};   // the TMA kernel's shape
+  hh::StagedShape shape_bulk{256, 2};    // per-thread bulk-copy kernel
   int last_launches = 0;
   // Host-buffer path.
   cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
@@ -135,25 +137,34 @@ int hash_device(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode, const
     return to_status(hh::launch_fixed_tma(b, ctx->shape_fixed, ctx->num_sms, stream));
   }
 
+  const bool sort = offsets != nullptr && ctx->kernel != HH_KERNEL_STAGED_UNSORTED &&
+                    n >= kSortMinMessages;
   hh::Queue q{};
-  q.tiles = (n + hh::kTileRows - 1) / hh::kTileRows;
-  bool aligned16 = false;
-  hh::StagedShape shape = ctx->shape_ragged;
-  if (offsets == nullptr) {
-    aligned16 = (reinterpret_cast<uintptr_t>(bytes) % 16 == 0) && (fixed_len % 16 == 0);
-  } else if (ctx->kernel != HH_KERNEL_STAGED_UNSORTED && n >= kSortMinMessages) {
+  if (sort) {
     if (n > kMaxSortedMessages) return HH_ERR_TOO_LARGE;
     int st = ensure_perm(ctx, n, stream);
     if (st != HH_OK) return st;
     int launches = 0;
     cudaError_t e = hh::launch_bucket_sort(offsets, n, ctx->d_hist, ctx->d_cursor, ctx->d_perm,
-                                           ctx->d_next_tile, ctx->num_sms, stream, &launches);
+                                           ctx->d_next_tile, ctx->d_use_perm, ctx->num_sms,
+                                           stream, &launches);
     ctx->last_launches += launches;
     if (e != cudaSuccess) return to_status(e);
     q.perm = ctx->d_perm;
+    q.use_perm = ctx->d_use_perm;
     q.next_tile = ctx->d_next_tile;
   }
-  cudaError_t e = hh::launch_staged(b, q, shape, aligned16, ctx->num_sms, stream);
+  cudaError_t e;
+  if (ctx->kernel == HH_KERNEL_STAGED_BULK) {
+    // Earlier design: 128-message CTA tiles, one bulk copy per thread.
+    q.tiles = (n + hh::kTileRows - 1) / hh::kTileRows;
+    const bool aligned16 = offsets == nullptr &&
+                           (reinterpret_cast<uintptr_t>(bytes) % 16 == 0) && (fixed_len % 16 == 0);
+    e = hh::launch_staged(b, q, ctx->shape_bulk, aligned16, ctx->num_sms, stream);
+  } else {
+    q.tiles = (n + 31) / 32;  // warp tiles
+    e = hh::launch_ragged(b, q, ctx->shape_ragged, ctx->num_sms, stream);
+  }
   ctx->last_launches += 1;
   return to_status(e);
 }
@@ -206,6 +217,7 @@ int hh_init(hh_ctx** out, int device, const char* tune_cache_path) {
   ctx->num_sms = prop.multiProcessorCount;
   bool ok = cudaMalloc(&ctx->d_err, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&ctx->d_next_tile, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc(&ctx->d_use_perm, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&ctx->d_hist, sizeof(uint32_t) * hh::kBuckets) == cudaSuccess &&
             cudaMalloc(&ctx->d_cursor, sizeof(uint32_t) * hh::kBuckets) == cudaSuccess &&
             cudaMemset(ctx->d_err, 0, sizeof(int)) == cudaSuccess &&
@@ -224,6 +236,7 @@ int hh_destroy(hh_ctx* ctx) {
   cudaDeviceSynchronize();
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_next_tile);
+  cudaFree(ctx->d_use_perm);
   cudaFree(ctx->d_hist);
   cudaFree(ctx->d_cursor);
   cudaFree(ctx->d_perm);
@@ -396,7 +409,7 @@ int hh_get_device_error(hh_ctx* ctx, void* stream) {
 }
 
 int hh_set_kernel(hh_ctx* ctx, int kernel) {
-  if (ctx == nullptr || kernel < HH_KERNEL_AUTO || kernel > HH_KERNEL_STAGED_UNSORTED)
+  if (ctx == nullptr || kernel < HH_KERNEL_AUTO || kernel > HH_KERNEL_STAGED_BULK)
     return HH_ERR_INVALID_ARG;
   ctx->kernel = kernel;
   return HH_OK;
@@ -417,15 +430,18 @@ int hh_update_microbench(hh_ctx* ctx, int variant, int64_t updates, int64_t thre
 }
 
 int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages) {
-  if (ctx == nullptr || (regime != HH_REGIME_FIXED && regime != HH_REGIME_RAGGED))
+  if (ctx == nullptr || regime < HH_REGIME_FIXED || regime > HH_REGIME_BULK)
     return HH_ERR_INVALID_ARG;
   const hh::StagedShape shape{window, stages};
   if (regime == HH_REGIME_FIXED) {
     if (!hh::fixed_shape_valid(shape)) return HH_ERR_INVALID_ARG;
     ctx->shape_fixed = shape;
+  } else if (regime == HH_REGIME_RAGGED) {
+    if (!hh::ragged_shape_valid(shape)) return HH_ERR_INVALID_ARG;
+    ctx->shape_ragged = shape;
   } else {
     if (hh::staged_smem_bytes(shape) == 0) return HH_ERR_INVALID_ARG;
-    ctx->shape_ragged = shape;
+    ctx->shape_bulk = shape;
   }
   return HH_OK;
 }

@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(kSortThreads) bucket_count_kernel(const int64_
 // cursor[k] = number of messages in buckets above k (descending order).
 __global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_t* hist,
                                                                    uint32_t* cursor,
-                                                                   unsigned long long* next_tile) {
+                                                                   unsigned long long* next_tile,
+                                                                   int* use_perm) {
   constexpr int kPer = kBuckets / kSortThreads;  // 4 buckets per thread
   __shared__ uint32_t warp_sums[kSortThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -102,11 +103,21 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_
     run += v[j];
   }
   if (tid == 0) *next_tile = 0ull;
+  // Buckets above kShortMax / 32 hold messages longer than kShortMax bytes.
+  const int long_bucket = kShortMax / 32 + 1;
+  bool mine = false;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j)
+    mine |= v[j] != 0 && kBuckets - 1 - (tid * kPer + j) >= long_bucket;
+  const int any_long = __syncthreads_or(mine);
+  if (tid == 0) *use_perm = any_long;
 }
 
 __global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(const int64_t* offsets,
                                                                       int64_t n, uint32_t* cursor,
-                                                                      int32_t* perm) {
+                                                                      int32_t* perm,
+                                                                      const int* use_perm) {
+  if (*use_perm == 0) return;
   __shared__ uint32_t cnt[kBuckets];
   __shared__ uint32_t base[kBuckets];
   const int lane = threadIdx.x & 31;
@@ -144,15 +155,15 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(const int6
 
 cudaError_t launch_bucket_sort(const int64_t* offsets, int64_t n, uint32_t* hist,
                                uint32_t* cursor, int32_t* perm, unsigned long long* next_tile,
-                               int num_sms, cudaStream_t stream, int* launches) {
+                               int* use_perm, int num_sms, cudaStream_t stream, int* launches) {
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kBuckets, stream);
   if (e != cudaSuccess) return e;
   const int64_t chunks = (n + kChunk - 1) / kChunk;
   const int64_t cap = static_cast<int64_t>(num_sms) * 2;
   const int grid = static_cast<int>(chunks < cap ? chunks : cap);
   bucket_count_kernel<<<grid, kSortThreads, 0, stream>>>(offsets, n, hist);
-  bucket_scan_kernel<<<1, kSortThreads, 0, stream>>>(hist, cursor, next_tile);
-  bucket_scatter_kernel<<<grid, kSortThreads, 0, stream>>>(offsets, n, cursor, perm);
+  bucket_scan_kernel<<<1, kSortThreads, 0, stream>>>(hist, cursor, next_tile, use_perm);
+  bucket_scatter_kernel<<<grid, kSortThreads, 0, stream>>>(offsets, n, cursor, perm, use_perm);
   *launches += 3;
   return cudaGetLastError();
 }

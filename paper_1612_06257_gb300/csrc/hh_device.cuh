@@ -115,7 +115,7 @@ __device__ __forceinline__ void zipper_pair(uint64_t a, uint64_t b, uint64_t& za
 //   4: as 3, and v1 += packet + mul0 on the FMA pipe as well.
 template <int V>
 __device__ __forceinline__ void update_v(State& s, const uint64_t p[4], uint32_t one) {
-  if (V == 0) {
+  if constexpr (V == 0) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       s.v1[i] += p[i] + s.mul0[i];
@@ -127,8 +127,7 @@ __device__ __forceinline__ void update_v(State& s, const uint64_t p[4], uint32_t
     zipper_add_pair(s.v0[2], s.v0[3], s.v1[2], s.v1[3]);
     zipper_add_pair(s.v1[0], s.v1[1], s.v0[0], s.v0[1]);
     zipper_add_pair(s.v1[2], s.v1[3], s.v0[2], s.v0[3]);
-    return;
-  }
+  } else {
   // V 1-2: add[i] = mul1 before its update (v0 + add + ZM(v1) is one 3-input
   // add later).  V 3-4: add[i] = v0 + mul1, formed now.
   uint64_t add[4];
@@ -156,6 +155,7 @@ __device__ __forceinline__ void update_v(State& s, const uint64_t p[4], uint32_t
   zipper_pair(s.v0[2], s.v0[3], z[2], z[3]);
 #pragma unroll
   for (int i = 0; i < 4; ++i) s.v1[i] = (V >= 2) ? add_on_fma(s.v1[i], z[i], one) : s.v1[i] + z[i];
+  }
 }
 
 // The variant every kernel uses: fastest in the Update-rate microbenchmark on
@@ -178,13 +178,9 @@ __device__ __forceinline__ void update_words(State& s, const uint32_t w[8]) {
 }
 
 // ---------------------------------------------------------------- Section 4.5
-// tail[0..7] hold the bytes that follow the last whole packet (only the first
-// r = size mod 32 bytes are meaningful; the rest may be anything).  For r != 0:
-// add (r << 32) + r to each lane of v0, rotate each 32-bit half of v1 left by
-// r, then Update with a packet that keeps the whole 4-byte groups of the tail
-// in place and puts the last r mod 4 bytes into bytes 28.. of the packet.
-__device__ __forceinline__ void remainder(State& s, uint32_t r, const uint32_t tail[8]) {
-  if (r == 0) return;
+// Size injection for r = size mod 32: add (r << 32) + r to each lane of v0
+// and rotate each 32-bit half of v1 left by r.  r == 0 changes nothing.
+__device__ __forceinline__ void inject_size(State& s, uint32_t r) {
   const uint64_t inject = (static_cast<uint64_t>(r) << 32) + r;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -192,8 +188,14 @@ __device__ __forceinline__ void remainder(State& s, uint32_t r, const uint32_t t
     const uint32_t lo = lo32(s.v1[i]), hi = hi32(s.v1[i]);
     s.v1[i] = join(__funnelshift_l(lo, lo, r), __funnelshift_l(hi, hi, r));
   }
+}
+
+// The padded packet of the last r bytes (tail[0..7] hold the bytes after the
+// last whole packet; only the first r are meaningful): whole 4-byte groups
+// stay in place, the last r mod 4 bytes go to bytes 28.., all else zero.
+__device__ __forceinline__ void remainder_packet(uint32_t r, const uint32_t tail[8],
+                                                 uint32_t pkt[8]) {
   const uint32_t whole = r >> 2, extra = r & 3;
-  uint32_t pkt[8];
   uint32_t last = 0;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -201,6 +203,13 @@ __device__ __forceinline__ void remainder(State& s, uint32_t r, const uint32_t t
     last = (static_cast<uint32_t>(j) == whole) ? tail[j] : last;
   }
   if (extra) pkt[7] |= last & ((1u << (8 * extra)) - 1u);
+}
+
+__device__ __forceinline__ void remainder(State& s, uint32_t r, const uint32_t tail[8]) {
+  if (r == 0) return;
+  inject_size(s, r);
+  uint32_t pkt[8];
+  remainder_packet(r, tail, pkt);
   update_words(s, pkt);
 }
 

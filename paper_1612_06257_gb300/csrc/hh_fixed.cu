@@ -51,8 +51,8 @@ struct FixedLayout {
 __device__ __forceinline__ void load_swizzled_packet(const uint8_t* box, int row, int chunk,
                                                      uint32_t w[8]) {
   const uint8_t* r = box + row * 128;
-  const uint4 a = *reinterpret_cast<const uint4*>(r + (((chunk) ^ (row & 7)) << 4));
-  const uint4 b = *reinterpret_cast<const uint4*>(r + (((chunk + 1) ^ (row & 7)) << 4));
+  const uint4 a = lds128(r + (((chunk) ^ (row & 7)) << 4));
+  const uint4 b = lds128(r + (((chunk + 1) ^ (row & 7)) << 4));
   w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
   w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
 }
@@ -84,18 +84,24 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
   }
   __syncthreads();
 
-  auto issue = [&](int64_t g) {
-    const int b = static_cast<int>(g % NST);
-    const int64_t tile = blockIdx.x + (g / steps) * gridDim.x;
-    const int32_t x0 = static_cast<int32_t>((g % steps) * W);
-    mbar_arrive_expect_tx(&full[b], L::kStageBytes);
+  // Producer cursor (thread 0 only): the (tile, window) of the next load.
+  int64_t p_tile = blockIdx.x, p_k = 0;
+  int p_buf = 0;
+  auto issue_next = [&]() {
+    mbar_arrive_expect_tx(&full[p_buf], L::kStageBytes);
 #pragma unroll
     for (int x = 0; x < kBoxes; ++x)
-      tma_load_2d(smem + b * L::kStageBytes + x * kBoxBytes, &tmap, x0 + 128 * x,
-                  static_cast<int32_t>(tile * kRows), &full[b]);
+      tma_load_2d(smem + p_buf * L::kStageBytes + x * kBoxBytes, &tmap,
+                  static_cast<int32_t>(p_k * W) + 128 * x, static_cast<int32_t>(p_tile * kRows),
+                  &full[p_buf]);
+    if (++p_k == steps) {
+      p_k = 0;
+      p_tile += gridDim.x;
+    }
+    p_buf = (p_buf + 1 == NST) ? 0 : p_buf + 1;
   };
   if (t == 0)
-    for (int64_t g = 0; g < NST && g < total; ++g) issue(g);
+    for (int64_t g = 0; g < NST && g < total; ++g) issue_next();
 
   const int64_t packets = p.len >> 5;
   const uint32_t r = static_cast<uint32_t>(p.len & 31);
@@ -107,53 +113,57 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
     for (int i = 0; i < 4; ++i) key[i] = __ldg(p.keys + i);
   }
   State s;
-  int64_t m = 0;
   bool ok = true;
-  for (int64_t g = 0; g < total; ++g) {
-    const int64_t k = g % steps;
-    if (k == 0) {
-      m = (blockIdx.x + (g / steps) * gridDim.x) * kRows + t;
-      if (p.per_message_keys) {
-        const uint64_t* kp = p.keys + 4 * (m < p.n ? m : 0);
+  int b = 0;                // stage buffer of the current window
+  uint32_t parity = 0;      // its phase parity
+  int64_t g = 0;            // position in this CTA's (tile, window) stream
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t m = tile * kRows + t;
+    if (p.per_message_keys) {
+      const uint64_t* kp = p.keys + 4 * (m < p.n ? m : 0);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
+      for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
+    }
+    init(s, key);
+    for (int64_t k = 0; k < steps; ++k, ++g) {
+      if (ok && !mbar_wait_bounded(&full[b], parity, kWaitLimitNs)) {
+        ok = false;
+        record_error(p.err, kErrTimeout);
       }
-      init(s, key);
-    }
-    const int b = static_cast<int>(g % NST);
-    const uint32_t parity = static_cast<uint32_t>((g / NST) & 1);
-    if (ok && !mbar_wait_bounded(&full[b], parity, kWaitLimitNs)) {
-      ok = false;
-      record_error(p.err, kErrTimeout);
-    }
-    const uint8_t* stage = smem + b * L::kStageBytes;
-    if (ok) {
-      const int64_t p0 = k * (W / 32);
+      const uint8_t* stage = smem + b * L::kStageBytes;
+      if (ok) {
+        const int64_t p0 = k * (W / 32);
 #pragma unroll
-      for (int j = 0; j < W / 32; ++j) {
-        if (p0 + j < packets) {
+        for (int j = 0; j < W / 32; ++j) {
+          if (p0 + j < packets) {
+            uint32_t w[8];
+            load_swizzled_packet(stage + (j / 4) * kBoxBytes, t, (j % 4) * 2, w);
+            update_words_v<kFastUpdate>(s, w, p.one);
+          }
+        }
+        if (k == rem_step) {
           uint32_t w[8];
-          load_swizzled_packet(stage + (j / 4) * kBoxBytes, t, (j % 4) * 2, w);
-          update_words_v<kFastUpdate>(s, w, p.one);
+          load_swizzled_packet(stage + (rem_off / 128) * kBoxBytes, t, (rem_off % 128) / 16, w);
+          remainder(s, r, w);
         }
       }
-      if (k == rem_step) {
-        uint32_t w[8];
-        load_swizzled_packet(stage + (rem_off / 128) * kBoxBytes, t, (rem_off % 128) / 16, w);
-        remainder(s, r, w);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[b]);
+      if (t == 0 && g + NST < total) {
+        // Refill this buffer once every warp has read it.
+        if (!mbar_wait_bounded(&empty[b], parity, kWaitLimitNs)) {
+          record_error(p.err, kErrTimeout);
+        } else {
+          fence_proxy_async_smem();
+          issue_next();
+        }
+      }
+      if (++b == NST) {
+        b = 0;
+        parity ^= 1u;
       }
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[b]);
-    if (t == 0 && g + NST < total) {
-      if (!mbar_wait_bounded(&empty[b], parity, kWaitLimitNs)) {
-        record_error(p.err, kErrTimeout);
-      } else {
-        fence_proxy_async_smem();
-        issue(g + NST);
-      }
-    }
-    if (k == steps - 1 && m < p.n) {
+    if (m < p.n) {
       finalize(s);
       uint64_t h[4];
       digest(s, h);

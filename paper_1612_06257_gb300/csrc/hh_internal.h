@@ -34,6 +34,7 @@ struct Batch {
 // Work-queue state of the staged kernel.
 struct Queue {
   const int32_t* perm;       // processing order of messages, or null = 0..n-1
+  const int* use_perm;       // device flag: 0 = ignore perm (no long message), or null
   unsigned long long* next_tile;  // atomic tile counter (sorted order), or null = static
   int64_t tiles;
 };
@@ -52,9 +53,16 @@ cudaError_t launch_staged(const Batch& b, const Queue& q, StagedShape shape, boo
 int staged_blocks_per_sm(StagedShape shape, bool aligned16);
 size_t staged_smem_bytes(StagedShape shape);
 
+// Ragged batches: warp tiles of 32 messages, coalesced cp.async staging.
+// Supported (window, stages) pairs:
+#define HH_RAGGED_SHAPES(X) X(128, 2) X(128, 3) X(128, 4) X(256, 2) X(256, 3)
+bool ragged_shape_valid(StagedShape shape);
+cudaError_t launch_ragged(const Batch& b, const Queue& q, StagedShape shape, int num_sms,
+                          cudaStream_t stream);
+
 // Fixed-length batches through 2D tensor-map TMA (len % 16 == 0, 16-byte
 // aligned bytes).  Supported (window, stages) pairs:
-#define HH_FIXED_SHAPES(X) X(128, 4) X(128, 6) X(256, 3)
+#define HH_FIXED_SHAPES(X) X(128, 2) X(128, 3) X(128, 4) X(128, 6) X(256, 2) X(256, 3)
 bool fixed_tma_supported(const uint8_t* bytes, int64_t len, int64_t n);
 cudaError_t launch_fixed_tma(const Batch& b, StagedShape shape, int num_sms, cudaStream_t stream);
 bool fixed_shape_valid(StagedShape shape);
@@ -64,8 +72,13 @@ cudaError_t launch_update_microbench(int variant, int64_t updates, int64_t threa
                                      uint64_t* out, cudaStream_t stream);
 
 // Length bucketing: hist and cursor are kBuckets words; perm n words.
+// The scan sets *use_perm = 1 when some message is longer than
+// kShortMax bytes (the order then matters for load balance), else 0 and the
+// scatter does nothing: all-short batches keep index order, which keeps their
+// loads sequential.
+constexpr int kShortMax = 64;
 cudaError_t launch_bucket_sort(const int64_t* offsets, int64_t n, uint32_t* hist,
                                uint32_t* cursor, int32_t* perm, unsigned long long* next_tile,
-                               int num_sms, cudaStream_t stream, int* launches);
+                               int* use_perm, int num_sms, cudaStream_t stream, int* launches);
 
 }  // namespace hh

@@ -120,8 +120,8 @@ template <bool kAligned>
 __device__ __forceinline__ void load_staged_packet(const uint8_t* row, uint32_t off,
                                                    uint32_t w[8]) {
   if (kAligned) {
-    const uint4 a = *reinterpret_cast<const uint4*>(row + off);
-    const uint4 c = *reinterpret_cast<const uint4*>(row + off + 16);
+    const uint4 a = lds128(row + off);
+    const uint4 c = lds128(row + off + 16);
     w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
     w[4] = c.x; w[5] = c.y; w[6] = c.z; w[7] = c.w;
   } else {

@@ -87,6 +87,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: far beyond any legitimate wait
 constexpr uint64_t kDrainLimitNs = 200000000ull;  // 0.2 s per buffer when giving up
 
+// 128-bit shared-memory load (kept as one LDS.128; the address must be
+// 16-byte aligned).
+__device__ __forceinline__ uint4 lds128(const void* p) {
+  uint4 v;
+  asm("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "r"(smem_u32(p)));
+  return v;
+}
+
 // 2D tiled tensor load (TMA) of one box at coordinates (x, y) into shared
 // memory, completing on an mbarrier.  x is the innermost (byte) coordinate.
 __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int32_t x, int32_t y,

@@ -1,0 +1,363 @@
+// hh_ragged.cu -- ragged batches: warp tiles, coalesced cp.async staging.
+//
+// Each warp owns a tile of 32 messages (one per lane; the 1024-bit state in
+// registers) and its own ring of NST shared-memory stages, each holding a
+// W-byte window of every message plus 16 bytes of alignment slack per row.
+// Warps never wait on one another: no CTA barrier, a warp-private ring, and
+// warp tiles taken from a queue (longest first after the length sort).
+//
+// Loading a stage: row r's window is the 16-byte aligned span around bytes
+// [kW, kW + W) of message r.  Four lanes copy each row, so one cp.async.cg
+// instruction moves 64 contiguous bytes of 8 rows (8 cache lines for 512
+// bytes); a row's base address and chunk range come from its owner lane by
+// shuffle, and chunk offsets fold into the instruction's immediate.  Only
+// the (at most two) partial 16-byte blocks at the two ends of the whole
+// batch are read bytewise, so no load leaves [offsets[0], offsets[n]).
+//
+// Reading a packet: when every message of the warp tile starts 16-byte
+// aligned, two 128-bit shared loads; otherwise nine 32-bit loads from the
+// enclosing words and one PRMT per word to shift the bytes into place.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hh_device.cuh"
+#include "hh_internal.h"
+#include "hh_ptx.cuh"
+
+namespace hh {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int W, int NST>
+struct RaggedLayout {
+  static constexpr int kStride = W + 16;             // bytes per row
+  static constexpr int kChunks = kStride / 16;       // 16-byte chunks per row
+  static constexpr int kPerLane = (kChunks + 3) / 4; // chunks per lane per row
+  static constexpr int kStageBytes = 32 * kStride;
+  static constexpr int kWarpBytes = NST * kStageBytes + 64;  // + read-past pad
+  static_assert((kStride / 4) % 32 == 4, "row stride must rotate 128-bit banks");
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ int64_t warp_max(int64_t v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const int64_t o = __shfl_xor_sync(kFull, v, d);
+    v = o > v ? o : v;
+  }
+  return v;
+}
+
+template <bool kAligned>
+__device__ __forceinline__ void read_packet(const uint8_t* row, uint32_t off, uint32_t w[8]) {
+  if (kAligned) {
+    const uint4 a = lds128(row + off);
+    const uint4 c = lds128(row + off + 16);
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    w[4] = c.x; w[5] = c.y; w[6] = c.z; w[7] = c.w;
+  } else {
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(row + (off & ~3u));
+    const uint32_t sel = 0x3210u + 0x1111u * (off & 3u);
+    uint32_t x[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) x[i] = p[i];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) w[j] = __byte_perm(x[j], x[j + 1], sel);
+  }
+}
+
+// Hash the packets of step k that this lane's message has, from its row.
+template <int W, bool kAligned>
+__device__ __forceinline__ void hash_step(State& s, const uint8_t* row, uint32_t mis, int64_t k,
+                                          int64_t packets, uint32_t r, int64_t rem_step,
+                                          uint32_t one) {
+  const int64_t p0 = k * (W / 32);
+#pragma unroll
+  for (int j = 0; j < W / 32; ++j) {
+    if (p0 + j < packets) {
+      uint32_t w[8];
+      read_packet<kAligned>(row, mis + 32u * j, w);
+      update_words_v<kFastUpdate>(s, w, one);
+    }
+  }
+  if (k == rem_step) {
+    uint32_t w[8];
+    read_packet<false>(row, mis + static_cast<uint32_t>(packets * 32 - k * W), w);
+    remainder(s, r, w);
+  }
+}
+
+// Messages of at most 64 bytes (a whole warp of them), read straight from
+// global memory: at most 17 aligned 32-bit words per message, shifted into
+// place with one PRMT per word.  Each message needs at most two data Updates
+// (update u exists when len > 32u; it is the padded remainder packet when
+// len < 32(u + 1)), so a warp runs at most two, whatever its length mix.
+// [lo_b, hi_b) is the batch's byte range: words that cross its ends are read
+// bytewise so that no load leaves it.
+__device__ __forceinline__ void hash_short(State& s, uintptr_t msg, uint32_t len, uintptr_t lo_b,
+                                           uintptr_t hi_b) {
+  const uintptr_t w0 = msg & ~uintptr_t(3);
+  const uint32_t b = static_cast<uint32_t>(msg & 3);
+  const uint32_t nwords = (b + len + 3) >> 2;  // <= 17
+  const uintptr_t lo4 = (lo_b + 3) & ~uintptr_t(3), hi4 = hi_b & ~uintptr_t(3);
+  uint32_t x[17];
+  if (w0 >= lo4 && w0 + 4 * nwords <= hi4) {
+#pragma unroll
+    for (int i = 0; i < 17; ++i)
+      x[i] = static_cast<uint32_t>(i) < nwords ? __ldg(reinterpret_cast<const uint32_t*>(w0) + i) : 0u;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 17; ++i) {
+      uint32_t v = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uintptr_t p = w0 + 4 * i + k;
+        if (static_cast<uint32_t>(i) < nwords && p >= lo_b && p < hi_b)
+          v |= static_cast<uint32_t>(*reinterpret_cast<const uint8_t*>(p)) << (8 * k);
+      }
+      x[i] = v;
+    }
+  }
+  const uint32_t sel = 0x3210u + 0x1111u * b;
+  uint32_t sw[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) sw[j] = __byte_perm(x[j], x[j + 1], sel);
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    if (len > 32u * u) {
+      const bool partial = len < 32u * (u + 1);
+      const uint32_t r = partial ? len - 32u * u : 0u;
+      if (partial) inject_size(s, r);
+      uint32_t tail[8], rp[8], pkt[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) tail[j] = sw[8 * u + j];
+      remainder_packet(r, tail, rp);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) pkt[j] = partial ? rp[j] : tail[j];
+      update_words(s, pkt);
+    }
+  }
+}
+
+template <int W, int NST, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
+  using L = RaggedLayout<W, NST>;
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint8_t* ring = smem + warp * L::kWarpBytes;
+  const uint32_t ring_s = smem_u32(ring);
+
+  const int64_t lo = b.offsets ? b.offsets[0] : 0;
+  const int64_t hi = b.offsets ? b.offsets[b.n] : b.n * b.fixed_len;
+  const uintptr_t base = reinterpret_cast<uintptr_t>(b.bytes);
+  const uintptr_t safe_lo = (base + lo + 15) & ~uintptr_t(15);
+  const uintptr_t safe_hi = (base + hi) & ~uintptr_t(15);
+
+  // Copy roles: lane = 4 * row_in_pass + part; pass h covers rows 8h..8h+7.
+  const int part = lane & 3;
+  const int row_in_pass = lane >> 2;
+
+  const int32_t* perm = (q.perm && (q.use_perm == nullptr || *q.use_perm)) ? q.perm : nullptr;
+  int64_t static_tile = static_cast<int64_t>(blockIdx.x) * WARPS + warp;
+  const int64_t static_step = static_cast<int64_t>(gridDim.x) * WARPS;
+
+  for (;;) {
+    int64_t tile;
+    if (q.next_tile) {
+      unsigned long long tk = 0;
+      if (lane == 0) tk = atomicAdd(q.next_tile, 1ull);
+      tile = static_cast<int64_t>(__shfl_sync(kFull, tk, 0));
+    } else {
+      tile = static_tile;
+      static_tile += static_step;
+    }
+    if (tile >= q.tiles) break;
+
+    const int64_t idx = tile * 32 + lane;
+    const bool valid = idx < b.n;
+    int64_t m = 0, start = 0, len = 0;
+    bool bad = false;
+    uint64_t key[4] = {0, 0, 0, 0};
+    if (valid) {
+      m = perm ? static_cast<int64_t>(perm[idx]) : idx;
+      if (b.offsets != nullptr) {
+        const int64_t s0 = b.offsets[m], e0 = b.offsets[m + 1];
+        bad = e0 < s0;
+        start = s0;
+        len = bad ? 0 : e0 - s0;
+        if (bad) record_error(b.err, kErrBadOffsets);
+      } else {
+        start = m * b.fixed_len;
+        len = b.fixed_len;
+      }
+      const uint64_t* kp = b.per_message_keys ? b.keys + 4 * m : b.keys;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
+    }
+    State s;
+    init(s, key);
+    if (__all_sync(kFull, len <= 64)) {
+      hash_short(s, base + start, static_cast<uint32_t>(len), base + lo, base + hi);
+      finalize(s);
+      if (valid) {
+        uint64_t h[4];
+        digest(s, h);
+        if (bad) h[0] = h[1] = h[2] = h[3] = 0;
+        uint64_t* o = b.out + m * b.words;
+        o[0] = h[0];
+        if (b.words >= 2) o[1] = h[1];
+        if (b.words == 4) {
+          o[2] = h[2];
+          o[3] = h[3];
+        }
+      }
+      continue;
+    }
+    const int64_t my_steps = (len + W - 1) / W;
+    const int64_t steps = warp_max(my_steps);
+    const uintptr_t msg = base + start;
+    const uint32_t mis = static_cast<uint32_t>(msg & 15);
+    const bool aligned = __all_sync(kFull, mis == 0);
+    const int64_t packets = len >> 5;
+    const uint32_t r = static_cast<uint32_t>(len & 31);
+    const int64_t rem_step = r ? (packets * 32) / W : -1;
+
+    // Stage k of all 32 rows into ring buffer (k % NST).
+    auto issue = [&](int64_t k, int buf) {
+      uint8_t* stage = ring + buf * L::kStageBytes;
+      // Owner side: this lane's window, as a 16-byte aligned chunk range.
+      uintptr_t a0 = 0;
+      uint32_t range = 0;  // first valid chunk | (end chunk << 8)
+      if (k < my_steps) {
+        const uintptr_t gs = msg + static_cast<uintptr_t>(k) * W;
+        const int64_t wend = k * W + W < len ? k * W + W : len;
+        const uintptr_t ge = msg + static_cast<uintptr_t>(wend);
+        a0 = gs & ~uintptr_t(15);
+        const uintptr_t a1 = (ge + 15) & ~uintptr_t(15);
+        const uintptr_t c0 = a0 > safe_lo ? a0 : safe_lo;
+        const uintptr_t c1 = a1 < safe_hi ? a1 : safe_hi;
+        uint32_t first = 0, end = 0;
+        if (c1 > c0) {
+          first = static_cast<uint32_t>((c0 - a0) >> 4);
+          end = static_cast<uint32_t>((c1 - a0) >> 4);
+        }
+        range = first | (end << 8);
+        if (c0 > gs || c1 < ge || c1 <= c0) {
+          // Bytes in the partial blocks at the batch ends: read bytewise.
+          uint8_t* row = stage + lane * L::kStride;
+          for (uintptr_t p = gs; p < ge; ++p)
+            if (p < c0 || p >= c1 || c1 <= c0) row[p - a0] = *reinterpret_cast<const uint8_t*>(p);
+        }
+      }
+      // Copier side: four lanes per row, eight rows per pass.
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int row = 8 * h + row_in_pass;
+        const uintptr_t rbase = static_cast<uintptr_t>(
+            __shfl_sync(kFull, static_cast<unsigned long long>(a0), row));
+        const uint32_t rr = __shfl_sync(kFull, range, row);
+        const uint32_t first = rr & 0xff, end = rr >> 8;
+        const char* src = reinterpret_cast<const char*>(rbase) + 16 * part;
+        const uint32_t dst = ring_s + buf * L::kStageBytes + row * L::kStride + 16 * part;
+#pragma unroll
+        for (int i = 0; i < L::kPerLane; ++i) {
+          const uint32_t c = part + 4 * i;
+          if (c >= first && c < end) cp_async16(dst + 64 * i, src + 64 * i);
+        }
+      }
+      cp_async_commit();
+    };
+
+    int buf_issue = 0, buf_read = 0;
+    for (int64_t k = 0; k < NST - 1; ++k) {
+      if (k < steps) issue(k, buf_issue);
+      else cp_async_commit();
+      buf_issue = (buf_issue + 1 == NST) ? 0 : buf_issue + 1;
+    }
+    for (int64_t k = 0; k < steps; ++k) {
+      if (k + NST - 1 < steps) issue(k + NST - 1, buf_issue);
+      else cp_async_commit();
+      buf_issue = (buf_issue + 1 == NST) ? 0 : buf_issue + 1;
+      cp_async_wait<NST - 1>();
+      __syncwarp();
+      if (k < my_steps) {
+        const uint8_t* row = ring + buf_read * L::kStageBytes + lane * L::kStride;
+        if (aligned)
+          hash_step<W, true>(s, row, 0u, k, packets, r, rem_step, 1u);
+        else
+          hash_step<W, false>(s, row, mis, k, packets, r, rem_step, 1u);
+      }
+      __syncwarp();  // every lane is done with this buffer before it refills
+      buf_read = (buf_read + 1 == NST) ? 0 : buf_read + 1;
+    }
+    cp_async_wait<0>();
+    finalize(s);
+    if (valid) {
+      uint64_t h[4];
+      digest(s, h);
+      if (bad) h[0] = h[1] = h[2] = h[3] = 0;
+      uint64_t* o = b.out + m * b.words;
+      o[0] = h[0];
+      if (b.words >= 2) o[1] = h[1];
+      if (b.words == 4) {
+        o[2] = h[2];
+        o[3] = h[3];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int W, int NST, int WARPS>
+cudaError_t launch_ragged_t(const Batch& b, const Queue& q, int num_sms, cudaStream_t stream) {
+  using L = RaggedLayout<W, NST>;
+  constexpr int kBytes = WARPS * L::kWarpBytes;
+  auto kern = ragged_kernel<W, NST, WARPS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, kBytes);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t blocks_needed = (q.tiles + WARPS - 1) / WARPS;
+  const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
+  const int grid = static_cast<int>(blocks_needed < cap ? blocks_needed : cap);
+  if (grid <= 0) return cudaSuccess;
+  kern<<<grid, WARPS * 32, kBytes, stream>>>(b, q);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool ragged_shape_valid(StagedShape shape) {
+#define HH_VALID(W_, N_) \
+  if (shape.window == W_ && shape.stages == N_) return true;
+  HH_RAGGED_SHAPES(HH_VALID)
+#undef HH_VALID
+  return false;
+}
+
+cudaError_t launch_ragged(const Batch& b, const Queue& q, StagedShape shape, int num_sms,
+                          cudaStream_t stream) {
+#define HH_RAGGED(W_, N_) \
+  if (shape.window == W_ && shape.stages == N_) return launch_ragged_t<W_, N_, 4>(b, q, num_sms, stream);
+  HH_RAGGED_SHAPES(HH_RAGGED)
+#undef HH_RAGGED
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace hh

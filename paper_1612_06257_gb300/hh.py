@@ -41,6 +41,7 @@ HH_KERNEL_AUTO = 0
 HH_KERNEL_NAIVE = 1
 HH_KERNEL_STAGED = 2
 HH_KERNEL_STAGED_UNSORTED = 3
+HH_KERNEL_STAGED_BULK = 4
 
 # Every symbol include/hh.h declares.
 EXPORTS = (
@@ -52,6 +53,7 @@ EXPORTS = (
 
 HH_REGIME_FIXED = 0
 HH_REGIME_RAGGED = 1
+HH_REGIME_BULK = 2
 
 _lock = threading.Lock()
 _lib = None

@@ -155,6 +155,23 @@ def test_offsets_not_starting_at_zero_and_exact_end(ctx):
         assert np.array_equal(run_ragged(ctx, shifted, 64, kernel), expect)
 
 
+@pytest.mark.parametrize("kernel", ["auto", "unsorted"])
+def test_short_messages_at_unaligned_batch_ends(ctx, kernel):
+    """All messages of 0..64 bytes (the direct-load path), with the byte
+    buffer starting 3 bytes into an allocation and ending mid-word, in a
+    batch large enough (1500) to run the length sort."""
+    g = torch.Generator().manual_seed(31)
+    lengths = torch.randint(0, 65, (1500,), generator=g)
+    lengths[0], lengths[-1] = 63, 61
+    w = workloads.from_lengths(lengths, seed=31, device=DEV)
+    backing = torch.zeros(w.total_bytes + 8, dtype=torch.uint8, device=DEV)
+    backing[3:3 + w.total_bytes] = w.data
+    view = backing[3:3 + w.total_bytes]
+    shifted = workloads.Workload("short", view, w.offsets, None, w.keys, True, w.n)
+    for bits in (64, 256):
+        assert np.array_equal(run_ragged(ctx, shifted, bits, kernel), oracle_hashes(w, bits))
+
+
 def test_output_guard_words_untouched(ctx):
     w = workloads.ragged(3000, seed=11, device=DEV, max_len=3000)
     out = torch.full((3000 * 2 + 64,), -0x5A5A5A5A5A5A5A5B, dtype=torch.int64, device=DEV)
