@@ -40,8 +40,8 @@ static uint64_t majority(uint64_t a, uint64_t b, uint64_t c) {
 }
 
 /* Section 4.4: a 256-bit number written most-significant word first, so the
- * first pi word is lane 3 and the "fourth number" is lane 0.  Lane 0 gets
- * every bit set that zero or one of the other three lanes have set, i.e.
+ * first pi word is lane 3 and the fourth word is lane 0.  Lane 0 gets
+ * every bit set that at most one of the other three lanes has set, i.e.
  * every bit where the other three do not hold a majority of ones. */
 static void make_constant(const uint64_t w[4], uint64_t c[4]) {
   c[3] = w[0];

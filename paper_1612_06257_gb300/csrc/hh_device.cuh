@@ -14,7 +14,7 @@ namespace hh {
 // ---------------------------------------------------------------- Section 4.4
 // The first eight 64-bit words of pi's hexadecimal fraction (3.243F6A88...).
 // Words 0-3 give the first constant, words 4-7 the second.  Written most
-// significant lane first, so word 0 is lane 3 and the "fourth number" lane 0;
+// significant lane first, so word 0 is lane 3 and the fourth word lane 0;
 // lane 0 then gets every bit that fewer than two of the other lanes have.
 // (A function rather than a table: device code cannot read a host array.)
 __host__ __device__ constexpr uint64_t pi_frac(int i) {

@@ -1,7 +1,7 @@
 """Hexadecimal digits of pi from Machin's formula, in exact integer arithmetic.
 
 pi = 16 atan(1/5) - 4 atan(1/239).  Used to pin the initialisation constants
-of Section 4.4 ("nothing up my sleeve" numbers taken from pi's hex digits)
+of Section 4.4 (openly derived numbers taken from pi's hex digits)
 without trusting any stored digit table.
 """
 

@@ -34,7 +34,7 @@ def test_constants_from_pi(oracle):
     for c, words in ((c0, w[0:4]), (c1, w[4:8])):
         # Lanes 3..1 hold the first three words unchanged.
         assert c[3] == words[0] and c[2] == words[1] and c[1] == words[2]
-        # Lane 0: the fourth word with every bit set that zero or one of the
+        # Lane 0: the fourth word with every bit set that at most one of the
         # other lanes have (counted bit by bit, not via a majority formula).
         expect = words[3]
         for bit in range(64):
