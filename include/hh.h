@@ -146,6 +146,38 @@ int hh_hash_host(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
                  const uint8_t* bytes, const int64_t* offsets, int64_t n, uint64_t* out);
 
 /*
+ * Ragged-batch hash that allocates nothing.  The paper has no counterpart: it
+ * serves callers that cannot allocate device memory for this library, because
+ * another allocator owns their device memory (a framework's caching pool, or
+ * a fixed budget that an out-of-band cudaMalloc would break) or because they
+ * run on a latency-critical path where cudaMalloc's implicit device
+ * synchronisation is not acceptable.
+ *
+ * Same hash and argument meaning as hh_hash{64,128,256}_batch (bits = 64,
+ * 128 or 256; device pointers; asynchronous on `stream`), on the current
+ * CUDA device, with no hh_ctx.  The length-sort scratch lives in a fixed
+ * file-scope device array of about 4.03 MiB (room for
+ * HH_NOALLOC_MAX_MESSAGES messages) that every GPU which loads the library
+ * holds until the process exits; n > HH_NOALLOC_MAX_MESSAGES returns
+ * HH_ERR_TOO_LARGE and enqueues nothing.  The call itself calls no
+ * cudaMalloc, cudaFree or allocating routine.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls on a device share the one array, so calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race
+ * and give wrong results: serialise them.  Each call clears or rewrites
+ * every part of the array it reads.  `device_error` is an optional device
+ * int: when the device detects an error (decreasing offsets) the first such
+ * hh_status code is written there; the call never clears it.  NULL
+ * discards device errors.
+ */
+#define HH_NOALLOC_MAX_MESSAGES (1 << 20)
+int hh_hash_batch_noalloc(int bits, const uint64_t* keys, int key_mode, const uint8_t* bytes,
+                          const int64_t* offsets, int64_t n, uint64_t* out, int* device_error,
+                          void* stream);
+
+/*
  * Synchronise `stream`, then return and clear the context's device error
  * word: HH_OK, HH_ERR_BAD_OFFSETS or HH_ERR_TIMEOUT (the first one recorded).
  */

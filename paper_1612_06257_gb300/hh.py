@@ -48,7 +48,7 @@ EXPORTS = (
     "hh_init", "hh_destroy", "hh_reserve", "hh_hash64_batch", "hh_hash128_batch",
     "hh_hash256_batch", "hh_hash_fixed", "hh_hash_host", "hh_get_device_error",
     "hh_set_kernel", "hh_last_launch_count", "hh_status_string", "hh_set_staged_shape",
-    "hh_update_microbench",
+    "hh_update_microbench", "hh_hash_batch_noalloc",
 )
 
 HH_REGIME_FIXED = 0
@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.hh_last_launch_count.argtypes = [_vp]
         L.hh_set_staged_shape.argtypes = [_vp, _int, _int, _int]
         L.hh_update_microbench.argtypes = [_vp, _int, _i64, _i64, _vp, _vp]
+        L.hh_hash_batch_noalloc.argtypes = [_int, _vp, _int, _vp, _vp, _i64, _vp, _vp, _vp]
         L.hh_status_string.argtypes = [_int]
         L.hh_status_string.restype = ctypes.c_char_p
         _lib = L
