@@ -194,12 +194,14 @@ enum hh_regime {
 };
 
 /* Set a kernel shape for one regime: `window` bytes of every message staged
- * per pipeline step and `stages` pipeline buffers.  Supported (window,
- * stages): HH_REGIME_FIXED (128, 2..4), (128, 6), (256, 2), (256, 3);
- * HH_REGIME_RAGGED (128, 2..4), (256, 2), (256, 3); HH_REGIME_BULK
- * (128, 3), (128, 4), (256, 2), (256, 3).  Other pairs return
- * HH_ERR_INVALID_ARG. */
-int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages);
+ * per pipeline step, `stages` pipeline buffers, and (fixed-length TMA kernel
+ * only; 1 elsewhere) `messages_per_thread` interleaved messages per thread.
+ * Supported (window, stages, messages_per_thread): HH_REGIME_FIXED
+ * (128, 2..4, 1), (256, 2..3, 1), (128, 2..3, 2); HH_REGIME_RAGGED
+ * (128, 2..4, 1), (256, 2..3, 1); HH_REGIME_BULK (128, 3..4, 1),
+ * (256, 2..3, 1).  Others return HH_ERR_INVALID_ARG. */
+int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages,
+                        int messages_per_thread);
 
 /*
  * Integer-issue microbenchmark (no counterpart in the paper; it measures the

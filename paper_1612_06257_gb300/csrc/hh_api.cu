@@ -61,7 +61,7 @@ struct hh_ctx {
   int32_t* d_perm = nullptr;
   int64_t perm_cap = 0;
   hh::StagedShape shape_ragged{256, 2};  // warp-tile kernel
-  hh::StagedShape shape_fixed{128, 3};   // the TMA kernel's shape
+  hh::StagedShape shape_fixed{128, 2, 2};  // the TMA kernel's shape
   hh::StagedShape shape_bulk{256, 2};    // per-thread bulk-copy kernel
   int last_launches = 0;
   // Host-buffer path.
@@ -429,10 +429,12 @@ int hh_update_microbench(hh_ctx* ctx, int variant, int64_t updates, int64_t thre
                                                 static_cast<cudaStream_t>(stream)));
 }
 
-int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages) {
+int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages,
+                        int messages_per_thread) {
   if (ctx == nullptr || regime < HH_REGIME_FIXED || regime > HH_REGIME_BULK)
     return HH_ERR_INVALID_ARG;
-  const hh::StagedShape shape{window, stages};
+  if (regime != HH_REGIME_FIXED && messages_per_thread != 1) return HH_ERR_INVALID_ARG;
+  const hh::StagedShape shape{window, stages, messages_per_thread};
   if (regime == HH_REGIME_FIXED) {
     if (!hh::fixed_shape_valid(shape)) return HH_ERR_INVALID_ARG;
     ctx->shape_fixed = shape;

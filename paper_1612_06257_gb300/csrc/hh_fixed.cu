@@ -41,9 +41,9 @@ struct FixedParams {
   uint32_t one;
 };
 
-template <int W, int NST>
+template <int W, int NST, int M>
 struct FixedLayout {
-  static constexpr int kStageBytes = W * kRows;
+  static constexpr int kStageBytes = W * kRows * M;
   static constexpr int kBarOffset = NST * kStageBytes;
   static constexpr int kBytes = kBarOffset + 2 * NST * 8 + 1024;  // + alignment slack
 };
@@ -57,11 +57,15 @@ __device__ __forceinline__ void load_swizzled_packet(const uint8_t* box, int row
   w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
 }
 
-template <int W, int NST>
+// M messages per thread: a tile is 128 * M messages; thread t hashes
+// messages t, t + 128, ... of the tile, interleaving M independent Update
+// chains for more instruction-level parallelism per warp.
+template <int W, int NST, int M>
 __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant__ CUtensorMap tmap,
                                                           FixedParams p) {
-  using L = FixedLayout<W, NST>;
+  using L = FixedLayout<W, NST, M>;
   constexpr int kBoxes = W / 128;
+  constexpr int kTileMsgs = kRows * M;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -70,7 +74,7 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
 
   const int t = threadIdx.x, lane = t & 31;
   const int64_t steps = (p.len + W - 1) / W;                 // windows per message (>= 1)
-  const int64_t tiles = (p.n + kRows - 1) / kRows;
+  const int64_t tiles = (p.n + kTileMsgs - 1) / kTileMsgs;
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = my_tiles * steps;                    // this CTA's (tile, window) stream
 
@@ -90,10 +94,12 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
   auto issue_next = [&]() {
     mbar_arrive_expect_tx(&full[p_buf], L::kStageBytes);
 #pragma unroll
-    for (int x = 0; x < kBoxes; ++x)
-      tma_load_2d(smem + p_buf * L::kStageBytes + x * kBoxBytes, &tmap,
-                  static_cast<int32_t>(p_k * W) + 128 * x, static_cast<int32_t>(p_tile * kRows),
-                  &full[p_buf]);
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+      for (int x = 0; x < kBoxes; ++x)
+        tma_load_2d(smem + p_buf * L::kStageBytes + (i * kBoxes + x) * kBoxBytes, &tmap,
+                    static_cast<int32_t>(p_k * W) + 128 * x,
+                    static_cast<int32_t>(p_tile * kTileMsgs + i * kRows), &full[p_buf]);
     if (++p_k == steps) {
       p_k = 0;
       p_tile += gridDim.x;
@@ -112,19 +118,23 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
 #pragma unroll
     for (int i = 0; i < 4; ++i) key[i] = __ldg(p.keys + i);
   }
-  State s;
+  State s[M];
   bool ok = true;
   int b = 0;                // stage buffer of the current window
   uint32_t parity = 0;      // its phase parity
   int64_t g = 0;            // position in this CTA's (tile, window) stream
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int64_t m = tile * kRows + t;
-    if (p.per_message_keys) {
-      const uint64_t* kp = p.keys + 4 * (m < p.n ? m : 0);
+    const int64_t m0 = tile * kTileMsgs + t;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
+    for (int i = 0; i < M; ++i) {
+      if (p.per_message_keys) {
+        const int64_t m = m0 + i * kRows;
+        const uint64_t* kp = p.keys + 4 * (m < p.n ? m : 0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) key[q] = __ldg(kp + q);
+      }
+      init(s[i], key);
     }
-    init(s, key);
     for (int64_t k = 0; k < steps; ++k, ++g) {
       if (ok && !mbar_wait_bounded(&full[b], parity, kWaitLimitNs)) {
         ok = false;
@@ -136,15 +146,22 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
 #pragma unroll
         for (int j = 0; j < W / 32; ++j) {
           if (p0 + j < packets) {
-            uint32_t w[8];
-            load_swizzled_packet(stage + (j / 4) * kBoxBytes, t, (j % 4) * 2, w);
-            update_words_v<kFastUpdate>(s, w, p.one);
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+              uint32_t w[8];
+              load_swizzled_packet(stage + (i * kBoxes + j / 4) * kBoxBytes, t, (j % 4) * 2, w);
+              update_words_v<kFastUpdate>(s[i], w, p.one);
+            }
           }
         }
         if (k == rem_step) {
-          uint32_t w[8];
-          load_swizzled_packet(stage + (rem_off / 128) * kBoxBytes, t, (rem_off % 128) / 16, w);
-          remainder(s, r, w);
+#pragma unroll
+          for (int i = 0; i < M; ++i) {
+            uint32_t w[8];
+            load_swizzled_packet(stage + (i * kBoxes + rem_off / 128) * kBoxBytes, t,
+                                 (rem_off % 128) / 16, w);
+            remainder(s[i], r, w);
+          }
         }
       }
       __syncwarp();
@@ -163,17 +180,22 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
         parity ^= 1u;
       }
     }
-    if (m < p.n) {
-      finalize(s);
-      uint64_t h[4];
-      digest(s, h);
-      if (!ok) h[0] = h[1] = h[2] = h[3] = 0;
-      uint64_t* o = p.out + m * p.words;
-      o[0] = h[0];
-      if (p.words >= 2) o[1] = h[1];
-      if (p.words == 4) {
-        o[2] = h[2];
-        o[3] = h[3];
+#pragma unroll
+    for (int i = 0; i < M; ++i) finalize(s[i]);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const int64_t m = m0 + i * kRows;
+      if (m < p.n) {
+        uint64_t h[4];
+        digest(s[i], h);
+        if (!ok) h[0] = h[1] = h[2] = h[3] = 0;
+        uint64_t* o = p.out + m * p.words;
+        o[0] = h[0];
+        if (p.words >= 2) o[1] = h[1];
+        if (p.words == 4) {
+          o[2] = h[2];
+          o[3] = h[3];
+        }
       }
     }
   }
@@ -204,18 +226,18 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-template <int W, int NST>
+template <int W, int NST, int M>
 cudaError_t launch_fixed_t(const CUtensorMap& tmap, const FixedParams& p, int num_sms,
                            cudaStream_t stream) {
-  using L = FixedLayout<W, NST>;
-  auto kern = fixed_tma_kernel<W, NST>;
+  using L = FixedLayout<W, NST, M>;
+  auto kern = fixed_tma_kernel<W, NST, M>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRows, L::kBytes);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  const int64_t tiles = (p.n + kRows - 1) / kRows;
+  const int64_t tiles = (p.n + kRows * M - 1) / (kRows * M);
   const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
   const int grid = static_cast<int>(tiles < cap ? tiles : cap);
   kern<<<grid, kRows, L::kBytes, stream>>>(tmap, p);
@@ -231,8 +253,8 @@ bool fixed_tma_supported(const uint8_t* bytes, int64_t len, int64_t n) {
 }
 
 bool fixed_shape_valid(StagedShape shape) {
-#define HH_VALID(W_, N_) \
-  if (shape.window == W_ && shape.stages == N_) return true;
+#define HH_VALID(W_, N_, M_) \
+  if (shape.window == W_ && shape.stages == N_ && shape.msgs == M_) return true;
   HH_FIXED_SHAPES(HH_VALID)
 #undef HH_VALID
   return false;
@@ -252,8 +274,9 @@ cudaError_t launch_fixed_tma(const Batch& b, StagedShape shape, int num_sms,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   FixedParams p{b.n, b.fixed_len, b.keys, b.per_message_keys, b.out, b.words, b.err, 1u};
-#define HH_FIXED(W_, N_) \
-  if (shape.window == W_ && shape.stages == N_) return launch_fixed_t<W_, N_>(tmap, p, num_sms, stream);
+#define HH_FIXED(W_, N_, M_)                                          \
+  if (shape.window == W_ && shape.stages == N_ && shape.msgs == M_) \
+    return launch_fixed_t<W_, N_, M_>(tmap, p, num_sms, stream);
   HH_FIXED_SHAPES(HH_FIXED)
 #undef HH_FIXED
   return cudaErrorInvalidValue;

@@ -42,8 +42,9 @@ struct Queue {
 // Staged-kernel shapes: bytes of each message staged per pipeline step (W)
 // and the number of pipeline buffers.
 struct StagedShape {
-  int window;   // 128 or 256
-  int stages;   // 2..4
+  int window;    // 128 or 256
+  int stages;    // 2..6
+  int msgs = 1;  // messages per thread (fixed-length TMA kernel)
 };
 
 // Launchers (return the CUDA error of the launch).
@@ -62,7 +63,8 @@ cudaError_t launch_ragged(const Batch& b, const Queue& q, StagedShape shape, int
 
 // Fixed-length batches through 2D tensor-map TMA (len % 16 == 0, 16-byte
 // aligned bytes).  Supported (window, stages) pairs:
-#define HH_FIXED_SHAPES(X) X(128, 2) X(128, 3) X(128, 4) X(128, 6) X(256, 2) X(256, 3)
+#define HH_FIXED_SHAPES(X) \
+  X(128, 2, 1) X(128, 3, 1) X(128, 4, 1) X(256, 2, 1) X(256, 3, 1) X(128, 2, 2) X(128, 3, 2)
 bool fixed_tma_supported(const uint8_t* bytes, int64_t len, int64_t n);
 cudaError_t launch_fixed_tma(const Batch& b, StagedShape shape, int num_sms, cudaStream_t stream);
 bool fixed_shape_valid(StagedShape shape);

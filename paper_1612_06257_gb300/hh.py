@@ -94,7 +94,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.hh_get_device_error.argtypes = [_vp, _vp]
         L.hh_set_kernel.argtypes = [_vp, _int]
         L.hh_last_launch_count.argtypes = [_vp]
-        L.hh_set_staged_shape.argtypes = [_vp, _int, _int, _int]
+        L.hh_set_staged_shape.argtypes = [_vp, _int, _int, _int, _int]
         L.hh_update_microbench.argtypes = [_vp, _int, _i64, _i64, _vp, _vp]
         L.hh_hash_batch_noalloc.argtypes = [_int, _vp, _int, _vp, _vp, _i64, _vp, _vp, _vp]
         L.hh_status_string.argtypes = [_int]
@@ -241,9 +241,10 @@ def hh_set_kernel(ctx, kernel: int) -> None:
     _check(load_library().hh_set_kernel(ctx.ptr, int(kernel)), "hh_set_kernel")
 
 
-def hh_set_staged_shape(ctx, regime: int, window: int, stages: int) -> None:
-    _check(load_library().hh_set_staged_shape(ctx.ptr, int(regime), int(window), int(stages)),
-           "hh_set_staged_shape")
+def hh_set_staged_shape(ctx, regime: int, window: int, stages: int,
+                        messages_per_thread: int = 1) -> None:
+    _check(load_library().hh_set_staged_shape(ctx.ptr, int(regime), int(window), int(stages),
+                                              int(messages_per_thread)), "hh_set_staged_shape")
 
 
 def hh_update_microbench(ctx, variant: int, updates: int, threads: int, out=None, stream=None):
