@@ -145,7 +145,7 @@ int hash_device(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode, const
     int st = ensure_perm(ctx, n, stream);
     if (st != HH_OK) return st;
     int launches = 0;
-    cudaError_t e = hh::launch_bucket_sort(offsets, n, ctx->d_hist, ctx->d_cursor, ctx->d_perm,
+    cudaError_t e = hh::launch_bucket_sort(offsets, bytes, n, ctx->d_hist, ctx->d_cursor, ctx->d_perm,
                                            ctx->d_next_tile, ctx->d_use_perm, ctx->num_sms,
                                            stream, &launches);
     ctx->last_launches += launches;
@@ -162,6 +162,16 @@ int hash_device(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode, const
                            (reinterpret_cast<uintptr_t>(bytes) % 16 == 0) && (fixed_len % 16 == 0);
     e = hh::launch_staged(b, q, ctx->shape_bulk, aligned16, ctx->num_sms, stream);
   } else {
+    if (sort) {
+      // All-short batches (the sort's flag says no message is longer than
+      // kShortMax) run in the short kernel; otherwise it returns at once and
+      // the warp-tile kernel runs.  Both are enqueued, so the sequence of
+      // launches does not depend on the data.
+      e = hh::launch_short(b, ctx->d_use_perm, ctx->num_sms, stream);
+      if (e != cudaSuccess) return to_status(e);
+      ctx->last_launches += 1;
+      q.skip_if_short = 1;
+    }
     q.tiles = (n + 31) / 32;  // warp tiles
     e = hh::launch_ragged(b, q, ctx->shape_ragged, ctx->num_sms, stream);
   }

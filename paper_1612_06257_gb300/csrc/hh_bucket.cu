@@ -1,11 +1,11 @@
 // hh_bucket.cu -- length bucketing of a ragged batch (work-queue order).
 //
-// A message of length L needs ceil(L / 32) Updates before finalisation (one
-// per whole 32-byte packet plus one for a partial packet, Sections 4.2 and
-// 4.5).  Messages are counting-sorted by that number, capped at kBuckets - 1,
-// in DESCENDING order, so that each 128-message tile of the staged kernel
-// holds messages of nearly equal length (no warp waits on one long message)
-// and tiles are handed out longest first (the long ones cannot end up last).
+// A message of length L needs P = ceil(L / 32) Updates before finalisation
+// (one per whole 32-byte packet plus one for a partial packet, Sections 4.2
+// and 4.5).  Messages are counting-sorted by P, capped at kBuckets - 1, in
+// DESCENDING order, so that a warp tile holds messages of equal Update count
+// (no lane waits on another) and tiles are handed out longest first (the
+// long ones cannot end up last).
 //
 // Three kernels: per-block histograms merged with one global atomic per
 // non-empty bucket; a one-block exclusive scan in descending bucket order
@@ -27,11 +27,11 @@ constexpr int kSortThreads = 1024;
 constexpr int kPerThread = 8;
 constexpr int kChunk = kSortThreads * kPerThread;
 
-__device__ __forceinline__ int bucket_of(const int64_t* offsets, int64_t i) {
+__device__ __forceinline__ int bucket_of(const int64_t* offsets, uintptr_t, int64_t i) {
   const int64_t len = offsets[i + 1] - offsets[i];
   if (len <= 0) return 0;  // empty, or invalid (reported by the hash kernel)
-  const int64_t k = (len + 31) >> 5;
-  return k >= kBuckets ? kBuckets - 1 : static_cast<int>(k);
+  const int64_t p = (len + 31) >> 5;
+  return p >= kBuckets ? kBuckets - 1 : static_cast<int>(p);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -41,7 +41,8 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 __global__ void __launch_bounds__(kSortThreads) bucket_count_kernel(const int64_t* offsets,
-                                                                    int64_t n, uint32_t* hist) {
+                                                                    uintptr_t base, int64_t n,
+                                                                    uint32_t* hist) {
   __shared__ uint32_t h[kBuckets];
   for (int i = threadIdx.x; i < kBuckets; i += kSortThreads) h[i] = 0;
   __syncthreads();
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(kSortThreads) bucket_count_kernel(const int64_
 #pragma unroll
     for (int e = 0; e < kPerThread; ++e) {
       const int64_t i = c + e * kSortThreads + threadIdx.x;
-      const int key = i < n ? bucket_of(offsets, i) : -1;
+      const int key = i < n ? bucket_of(offsets, base, i) : -1;
       const unsigned peers = __match_any_sync(0xffffffffu, key);
       if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[key], __popc(peers));
     }
@@ -114,7 +115,8 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_
 }
 
 __global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(const int64_t* offsets,
-                                                                      int64_t n, uint32_t* cursor,
+                                                                      uintptr_t byte_base, int64_t n,
+                                                                      uint32_t* cursor,
                                                                       int32_t* perm,
                                                                       const int* use_perm) {
   if (*use_perm == 0) return;
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(const int6
 #pragma unroll
     for (int e = 0; e < kPerThread; ++e) {
       const int64_t i = c + e * kSortThreads + threadIdx.x;
-      key[e] = i < n ? bucket_of(offsets, i) : -1;
+      key[e] = i < n ? bucket_of(offsets, byte_base, i) : -1;
       const unsigned peers = __match_any_sync(0xffffffffu, key[e]);
       const int leader = __ffs(peers) - 1;
       uint32_t first = 0;
@@ -153,7 +155,8 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(const int6
 
 }  // namespace
 
-cudaError_t launch_bucket_sort(const int64_t* offsets, int64_t n, uint32_t* hist,
+cudaError_t launch_bucket_sort(const int64_t* offsets, const uint8_t* bytes, int64_t n,
+                               uint32_t* hist,
                                uint32_t* cursor, int32_t* perm, unsigned long long* next_tile,
                                int* use_perm, int num_sms, cudaStream_t stream, int* launches) {
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kBuckets, stream);
@@ -161,9 +164,11 @@ cudaError_t launch_bucket_sort(const int64_t* offsets, int64_t n, uint32_t* hist
   const int64_t chunks = (n + kChunk - 1) / kChunk;
   const int64_t cap = static_cast<int64_t>(num_sms) * 2;
   const int grid = static_cast<int>(chunks < cap ? chunks : cap);
-  bucket_count_kernel<<<grid, kSortThreads, 0, stream>>>(offsets, n, hist);
+  const uintptr_t base = reinterpret_cast<uintptr_t>(bytes);
+  bucket_count_kernel<<<grid, kSortThreads, 0, stream>>>(offsets, base, n, hist);
   bucket_scan_kernel<<<1, kSortThreads, 0, stream>>>(hist, cursor, next_tile, use_perm);
-  bucket_scatter_kernel<<<grid, kSortThreads, 0, stream>>>(offsets, n, cursor, perm, use_perm);
+  bucket_scatter_kernel<<<grid, kSortThreads, 0, stream>>>(offsets, base, n, cursor, perm,
+                                                           use_perm);
   *launches += 3;
   return cudaGetLastError();
 }

@@ -11,7 +11,7 @@ namespace hh {
 constexpr int kErrTimeout = 4;
 constexpr int kErrBadOffsets = 6;
 
-// Length-sort buckets: bucket = min(ceil(len / 32), kBuckets - 1), i.e. the
+// Length-sort buckets: bucket = min(ceil(len / 32), kBuckets - 1), the
 // number of Updates a message needs before finalisation, capped.
 constexpr int kBuckets = 4096;
 
@@ -35,6 +35,7 @@ struct Batch {
 struct Queue {
   const int32_t* perm;       // processing order of messages, or null = 0..n-1
   const int* use_perm;       // device flag: 0 = ignore perm (no long message), or null
+  int skip_if_short = 0;     // 1: return at once when *use_perm == 0 (the short kernel runs)
   unsigned long long* next_tile;  // atomic tile counter (sorted order), or null = static
   int64_t tiles;
 };
@@ -61,6 +62,10 @@ bool ragged_shape_valid(StagedShape shape);
 cudaError_t launch_ragged(const Batch& b, const Queue& q, StagedShape shape, int num_sms,
                           cudaStream_t stream);
 
+// Batches of messages of at most kShortMax bytes: thread per message, no
+// shared memory.  Returns at once unless *run_if == 0 (run_if may be null).
+cudaError_t launch_short(const Batch& b, const int* run_if, int num_sms, cudaStream_t stream);
+
 // Fixed-length batches through 2D tensor-map TMA (len % 16 == 0, 16-byte
 // aligned bytes).  Supported (window, stages) pairs:
 #define HH_FIXED_SHAPES(X) \
@@ -79,7 +84,8 @@ cudaError_t launch_update_microbench(int variant, int64_t updates, int64_t threa
 // scatter does nothing: all-short batches keep index order, which keeps their
 // loads sequential.
 constexpr int kShortMax = 64;
-cudaError_t launch_bucket_sort(const int64_t* offsets, int64_t n, uint32_t* hist,
+cudaError_t launch_bucket_sort(const int64_t* offsets, const uint8_t* bytes, int64_t n,
+                               uint32_t* hist,
                                uint32_t* cursor, int32_t* perm, unsigned long long* next_tile,
                                int* use_perm, int num_sms, cudaStream_t stream, int* launches);
 

@@ -115,7 +115,12 @@ __device__ __forceinline__ void hash_short(State& s, uintptr_t msg, uint32_t len
   const uint32_t nwords = (b + len + 3) >> 2;  // <= 17
   const uintptr_t lo4 = (lo_b + 3) & ~uintptr_t(3), hi4 = hi_b & ~uintptr_t(3);
   uint32_t x[17];
-  if (w0 >= lo4 && w0 + 4 * nwords <= hi4) {
+  if (w0 >= lo4 && w0 + 68 <= hi4) {
+    // All 17 words lie inside the batch: load them without per-word tests
+    // (words past the message are ignored below).
+#pragma unroll
+    for (int i = 0; i < 17; ++i) x[i] = __ldg(reinterpret_cast<const uint32_t*>(w0) + i);
+  } else if (w0 >= lo4 && w0 + 4 * nwords <= hi4) {
 #pragma unroll
     for (int i = 0; i < 17; ++i)
       x[i] = static_cast<uint32_t>(i) < nwords ? __ldg(reinterpret_cast<const uint32_t*>(w0) + i) : 0u;
@@ -171,6 +176,7 @@ __global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
   const int part = lane & 3;
   const int row_in_pass = lane >> 2;
 
+  if (q.skip_if_short && q.use_perm != nullptr && *q.use_perm == 0) return;  // short kernel runs
   const int32_t* perm = (q.perm && (q.use_perm == nullptr || *q.use_perm)) ? q.perm : nullptr;
   int64_t static_tile = static_cast<int64_t>(blockIdx.x) * WARPS + warp;
   const int64_t static_step = static_cast<int64_t>(gridDim.x) * WARPS;
@@ -231,7 +237,7 @@ __global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
     const int64_t steps = warp_max(my_steps);
     const uintptr_t msg = base + start;
     const uint32_t mis = static_cast<uint32_t>(msg & 15);
-    const bool aligned = __all_sync(kFull, mis == 0);
+    const bool aligned = __all_sync(kFull, mis == 0 || !valid);
     const int64_t packets = len >> 5;
     const uint32_t r = static_cast<uint32_t>(len & 31);
     const int64_t rem_step = r ? (packets * 32) / W : -1;
@@ -296,7 +302,7 @@ __global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
       __syncwarp();
       if (k < my_steps) {
         const uint8_t* row = ring + buf_read * L::kStageBytes + lane * L::kStride;
-        if (aligned)
+        if (aligned)  // warp-uniform
           hash_step<W, true>(s, row, 0u, k, packets, r, rem_step, 1u);
         else
           hash_step<W, false>(s, row, mis, k, packets, r, rem_step, 1u);
@@ -322,6 +328,46 @@ __global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
   }
 }
 
+// Thread per message for batches whose messages are all at most kShortMax
+// bytes, in index order (neighbouring threads read neighbouring bytes), with
+// no shared memory so that occupancy is set by registers alone.
+__global__ void __launch_bounds__(256) short_kernel(Batch b, const int* run_if) {
+  if (run_if != nullptr && *run_if != 0) return;
+  const int64_t lo = b.offsets[0], hi = b.offsets[b.n];
+  const uintptr_t base = reinterpret_cast<uintptr_t>(b.bytes);
+  uint64_t key[4];
+  if (!b.per_message_keys) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) key[i] = __ldg(b.keys + i);
+  }
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; m < b.n;
+       m += stride) {
+    const int64_t s0 = b.offsets[m], e0 = b.offsets[m + 1];
+    const bool bad = e0 < s0;
+    if (bad) record_error(b.err, kErrBadOffsets);
+    const int64_t len = bad ? 0 : (e0 - s0 < kShortMax ? e0 - s0 : kShortMax);
+    if (b.per_message_keys) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) key[i] = __ldg(b.keys + 4 * m + i);
+    }
+    State s;
+    init(s, key);
+    hash_short(s, base + s0, static_cast<uint32_t>(len), base + lo, base + hi);
+    finalize(s);
+    uint64_t h[4];
+    digest(s, h);
+    if (bad) h[0] = h[1] = h[2] = h[3] = 0;
+    uint64_t* o = b.out + m * b.words;
+    o[0] = h[0];
+    if (b.words >= 2) o[1] = h[1];
+    if (b.words == 4) {
+      o[2] = h[2];
+      o[3] = h[3];
+    }
+  }
+}
+
 template <int W, int NST, int WARPS>
 cudaError_t launch_ragged_t(const Batch& b, const Queue& q, int num_sms, cudaStream_t stream) {
   using L = RaggedLayout<W, NST>;
@@ -342,6 +388,19 @@ cudaError_t launch_ragged_t(const Batch& b, const Queue& q, int num_sms, cudaStr
 }
 
 }  // namespace
+
+cudaError_t launch_short(const Batch& b, const int* run_if, int num_sms, cudaStream_t stream) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, short_kernel, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t blocks = (b.n + 255) / 256;
+  const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
+  const int grid = static_cast<int>(blocks < cap ? blocks : cap);
+  if (grid <= 0) return cudaSuccess;
+  short_kernel<<<grid, 256, 0, stream>>>(b, run_if);
+  return cudaGetLastError();
+}
 
 bool ragged_shape_valid(StagedShape shape) {
 #define HH_VALID(W_, N_) \
