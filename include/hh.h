@@ -59,7 +59,8 @@ enum hh_status {
   HH_ERR_TIMEOUT = 4,       /* device: a bounded pipeline wait ran out        */
   HH_ERR_TOO_LARGE = 5,     /* a size beyond what the call supports           */
   HH_ERR_BAD_OFFSETS = 6,   /* device: offsets[i+1] < offsets[i] somewhere    */
-  HH_ERR_NO_DEVICE = 7      /* no usable CUDA device with sm_103a             */
+  HH_ERR_NO_DEVICE = 7,     /* no usable CUDA device with sm_103a             */
+  HH_ERR_BAD_KEY_INDEX = 8  /* device: a key index outside the key table      */
 };
 
 /* How `keys` is laid out. */
@@ -135,6 +136,32 @@ int hh_hash_fixed(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
                   void* stream);
 
 /*
+ * Hash a batch given as segments of one byte buffer, each with its own key
+ * from a device key table: the batch descriptor of a request server, where
+ * messages of many requests share one launch.
+ *   key_table  uint64[key_count][4]; key_index int32[n] picks message i's
+ *              row (NULL: every message uses row 0).  An index outside
+ *              [0, key_count) sets HH_ERR_BAD_KEY_INDEX on the device and the
+ *              message's output words are written as zero.
+ *   bytes      a buffer of bytes_len bytes (not NULL); message i is
+ *              bytes[starts[i] .. starts[i] + lengths[i]).  Segments may come
+ *              in any order and may overlap.  A segment that does not lie in
+ *              [0, bytes_len) sets HH_ERR_BAD_OFFSETS and gets zero output.
+ *              The library reads only bytes inside [0, bytes_len).
+ *   n_device   NULL, or a device int64 holding the message count at run time;
+ *              then n is only a capacity (the arrays hold n entries) and
+ *              the launch configuration depends on n alone, so one captured
+ *              launch serves batches of any size up to n.  Reserve scratch
+ *              for n messages (hh_reserve) before capturing.
+ *   out        uint64[n * bits/64] as for the ragged calls.
+ * Same hash (Sections 4.2-4.5), asynchronous on `stream`.
+ */
+int hh_hash_segments(hh_ctx* ctx, int bits, const uint64_t* key_table, int32_t key_count,
+                     const int32_t* key_index, const uint8_t* bytes, int64_t bytes_len,
+                     const int64_t* starts, const int64_t* lengths, int64_t n,
+                     const int64_t* n_device, uint64_t* out, void* stream);
+
+/*
  * Host-memory variant of the ragged call: keys, bytes, offsets and out are
  * HOST pointers (pinned memory gives full copy speed; pageable works).  The
  * batch is copied to the device in chunks, hashed there and copied back,
@@ -179,7 +206,8 @@ int hh_hash_batch_noalloc(int bits, const uint64_t* keys, int key_mode, const ui
 
 /*
  * Synchronise `stream`, then return and clear the context's device error
- * word: HH_OK, HH_ERR_BAD_OFFSETS or HH_ERR_TIMEOUT (the first one recorded).
+ * word: HH_OK, HH_ERR_BAD_OFFSETS, HH_ERR_BAD_KEY_INDEX or HH_ERR_TIMEOUT
+ * (the first one recorded).
  */
 int hh_get_device_error(hh_ctx* ctx, void* stream);
 

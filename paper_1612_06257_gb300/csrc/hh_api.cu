@@ -98,54 +98,34 @@ int ensure_perm(hh_ctx* ctx, int64_t n, cudaStream_t stream) {
 
 int words_of(int bits) { return bits == 64 ? 1 : bits == 128 ? 2 : bits == 256 ? 4 : 0; }
 
-// One device-pointer batch, ragged (offsets != null) or fixed-length.
-int hash_device(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode, const uint8_t* bytes,
-                const int64_t* offsets, int64_t fixed_len, int64_t n, uint64_t* out,
-                cudaStream_t stream) {
-  if (ctx == nullptr) return HH_ERR_INVALID_ARG;
-  const int words = words_of(bits);
-  if (words == 0 || (key_mode != HH_KEY_SHARED && key_mode != HH_KEY_PER_MESSAGE) || n < 0 ||
-      fixed_len < 0)
-    return HH_ERR_INVALID_ARG;
+// Enqueue the hash of one device batch `b` (offsets, fixed or segments
+// form; the caller has checked its arguments and filled b).
+int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
   ctx->last_launches = 0;
-  if (n == 0) return HH_OK;
-  if (keys == nullptr || out == nullptr) return HH_ERR_INVALID_ARG;
-  // Only a fixed-length batch of empty messages may come without bytes.
-  if (bytes == nullptr && !(offsets == nullptr && fixed_len == 0)) return HH_ERR_INVALID_ARG;
-  if (offsets == nullptr && fixed_len > 0 && n > INT64_MAX / fixed_len) return HH_ERR_TOO_LARGE;
+  if (b.n == 0) return HH_OK;
   DeviceGuard guard(ctx->device);
   if (!guard.ok) return HH_ERR_CUDA;
-
-  hh::Batch b{};
-  b.bytes = bytes;
-  b.offsets = offsets;
-  b.fixed_len = fixed_len;
-  b.keys = keys;
-  b.per_message_keys = key_mode == HH_KEY_PER_MESSAGE;
-  b.n = n;
-  b.out = out;
-  b.words = words;
   b.err = ctx->d_err;
+  const int64_t n = b.n;
+  const bool fixed = b.offsets == nullptr && b.seg_start == nullptr;
 
   if (ctx->kernel == HH_KERNEL_NAIVE) {
     ctx->last_launches = 1;
     return to_status(hh::launch_naive(b, stream));
   }
-
-  if (offsets == nullptr && hh::fixed_tma_supported(bytes, fixed_len, n)) {
+  if (fixed && b.key_index == nullptr && hh::fixed_tma_supported(b.bytes, b.fixed_len, n)) {
     ctx->last_launches = 1;
     return to_status(hh::launch_fixed_tma(b, ctx->shape_fixed, ctx->num_sms, stream));
   }
 
-  const bool sort = offsets != nullptr && ctx->kernel != HH_KERNEL_STAGED_UNSORTED &&
-                    n >= kSortMinMessages;
+  const bool sort = !fixed && ctx->kernel != HH_KERNEL_STAGED_UNSORTED && n >= kSortMinMessages;
   hh::Queue q{};
   if (sort) {
     if (n > kMaxSortedMessages) return HH_ERR_TOO_LARGE;
     int st = ensure_perm(ctx, n, stream);
     if (st != HH_OK) return st;
     int launches = 0;
-    cudaError_t e = hh::launch_bucket_sort(offsets, bytes, n, ctx->d_hist, ctx->d_cursor, ctx->d_perm,
+    cudaError_t e = hh::launch_bucket_sort(b, ctx->d_hist, ctx->d_cursor, ctx->d_perm,
                                            ctx->d_next_tile, ctx->d_use_perm, ctx->num_sms,
                                            stream, &launches);
     ctx->last_launches += launches;
@@ -158,8 +138,8 @@ int hash_device(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode, const
   if (ctx->kernel == HH_KERNEL_STAGED_BULK) {
     // Earlier design: 128-message CTA tiles, one bulk copy per thread.
     q.tiles = (n + hh::kTileRows - 1) / hh::kTileRows;
-    const bool aligned16 = offsets == nullptr &&
-                           (reinterpret_cast<uintptr_t>(bytes) % 16 == 0) && (fixed_len % 16 == 0);
+    const bool aligned16 = fixed && (reinterpret_cast<uintptr_t>(b.bytes) % 16 == 0) &&
+                           (b.fixed_len % 16 == 0);
     e = hh::launch_staged(b, q, ctx->shape_bulk, aligned16, ctx->num_sms, stream);
   } else {
     if (sort) {
@@ -177,6 +157,33 @@ int hash_device(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode, const
   }
   ctx->last_launches += 1;
   return to_status(e);
+}
+
+// Argument checks and Batch set-up shared by the offsets and fixed forms.
+int hash_common(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode, const uint8_t* bytes,
+                const int64_t* offsets, int64_t fixed_len, int64_t n, uint64_t* out,
+                cudaStream_t stream) {
+  if (ctx == nullptr) return HH_ERR_INVALID_ARG;
+  const int words = words_of(bits);
+  if (words == 0 || (key_mode != HH_KEY_SHARED && key_mode != HH_KEY_PER_MESSAGE) || n < 0 ||
+      fixed_len < 0)
+    return HH_ERR_INVALID_ARG;
+  ctx->last_launches = 0;
+  if (n == 0) return HH_OK;
+  if (keys == nullptr || out == nullptr) return HH_ERR_INVALID_ARG;
+  // Only a fixed-length batch of empty messages may come without bytes.
+  if (bytes == nullptr && !(offsets == nullptr && fixed_len == 0)) return HH_ERR_INVALID_ARG;
+  if (offsets == nullptr && fixed_len > 0 && n > INT64_MAX / fixed_len) return HH_ERR_TOO_LARGE;
+  hh::Batch b{};
+  b.bytes = bytes;
+  b.offsets = offsets;
+  b.fixed_len = fixed_len;
+  b.keys = keys;
+  b.per_message_keys = key_mode == HH_KEY_PER_MESSAGE;
+  b.n = n;
+  b.out = out;
+  b.words = words;
+  return hash_device(ctx, b, stream);
 }
 
 template <typename T>
@@ -205,6 +212,7 @@ const char* hh_status_string(int status) {
     case HH_ERR_TOO_LARGE: return "size too large for this call";
     case HH_ERR_BAD_OFFSETS: return "offsets decrease";
     case HH_ERR_NO_DEVICE: return "no usable sm_103 CUDA device";
+    case HH_ERR_BAD_KEY_INDEX: return "key index outside the key table";
     default: return "unknown status";
   }
 }
@@ -277,21 +285,21 @@ int hh_reserve(hh_ctx* ctx, int64_t max_messages) {
 int hh_hash64_batch(hh_ctx* ctx, const uint64_t* keys, int key_mode, const uint8_t* bytes,
                     const int64_t* offsets, int64_t n, uint64_t* out, void* stream) {
   if (offsets == nullptr && n > 0) return HH_ERR_INVALID_ARG;
-  return hash_device(ctx, 64, keys, key_mode, bytes, offsets, 0, n, out,
+  return hash_common(ctx, 64, keys, key_mode, bytes, offsets, 0, n, out,
                      static_cast<cudaStream_t>(stream));
 }
 
 int hh_hash128_batch(hh_ctx* ctx, const uint64_t* keys, int key_mode, const uint8_t* bytes,
                      const int64_t* offsets, int64_t n, uint64_t* out, void* stream) {
   if (offsets == nullptr && n > 0) return HH_ERR_INVALID_ARG;
-  return hash_device(ctx, 128, keys, key_mode, bytes, offsets, 0, n, out,
+  return hash_common(ctx, 128, keys, key_mode, bytes, offsets, 0, n, out,
                      static_cast<cudaStream_t>(stream));
 }
 
 int hh_hash256_batch(hh_ctx* ctx, const uint64_t* keys, int key_mode, const uint8_t* bytes,
                      const int64_t* offsets, int64_t n, uint64_t* out, void* stream) {
   if (offsets == nullptr && n > 0) return HH_ERR_INVALID_ARG;
-  return hash_device(ctx, 256, keys, key_mode, bytes, offsets, 0, n, out,
+  return hash_common(ctx, 256, keys, key_mode, bytes, offsets, 0, n, out,
                      static_cast<cudaStream_t>(stream));
 }
 
@@ -299,8 +307,36 @@ int hh_hash_fixed(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
                   const uint8_t* bytes, int64_t msg_len, int64_t n, uint64_t* out,
                   void* stream) {
   if (msg_len < 0) return HH_ERR_INVALID_ARG;
-  return hash_device(ctx, bits, keys, key_mode, bytes, nullptr, msg_len, n, out,
+  return hash_common(ctx, bits, keys, key_mode, bytes, nullptr, msg_len, n, out,
                      static_cast<cudaStream_t>(stream));
+}
+
+int hh_hash_segments(hh_ctx* ctx, int bits, const uint64_t* key_table, int32_t key_count,
+                     const int32_t* key_index, const uint8_t* bytes, int64_t bytes_len,
+                     const int64_t* starts, const int64_t* lengths, int64_t n,
+                     const int64_t* n_device, uint64_t* out, void* stream) {
+  if (ctx == nullptr) return HH_ERR_INVALID_ARG;
+  const int words = words_of(bits);
+  if (words == 0 || n < 0 || bytes_len < 0 || key_count < 1) return HH_ERR_INVALID_ARG;
+  ctx->last_launches = 0;
+  if (n == 0) return HH_OK;
+  if (key_table == nullptr || starts == nullptr || lengths == nullptr || out == nullptr ||
+      bytes == nullptr)
+    return HH_ERR_INVALID_ARG;
+  hh::Batch b{};
+  b.bytes = bytes;
+  b.seg_start = starts;
+  b.seg_len = lengths;
+  b.bytes_len = bytes_len;
+  b.keys = key_table;
+  b.per_message_keys = 0;
+  b.key_index = key_index;
+  b.key_count = key_count;
+  b.n = n;
+  b.n_dev = n_device;
+  b.out = out;
+  b.words = words;
+  return hash_device(ctx, b, static_cast<cudaStream_t>(stream));
 }
 
 int hh_hash_host(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
@@ -380,7 +416,7 @@ int hh_hash_host(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
     // The device offsets are absolute; shift the base so that
     // base + offsets[m0] is the first staged byte.
     const uint8_t* dev_base = s.bytes - offsets[m0];
-    int st = hash_device(ctx, bits, s.keys, key_mode, dev_base, s.offsets, 0, cn, s.out,
+    int st = hash_common(ctx, bits, s.keys, key_mode, dev_base, s.offsets, 0, cn, s.out,
                          ctx->s_comp);
     launches += ctx->last_launches;
     if (st != HH_OK) return st;

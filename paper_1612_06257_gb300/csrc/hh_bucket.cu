@@ -18,6 +18,7 @@
 
 #include <cstdint>
 
+#include "hh_batch.cuh"
 #include "hh_internal.h"
 
 namespace hh {
@@ -27,8 +28,8 @@ constexpr int kSortThreads = 1024;
 constexpr int kPerThread = 8;
 constexpr int kChunk = kSortThreads * kPerThread;
 
-__device__ __forceinline__ int bucket_of(const int64_t* offsets, uintptr_t, int64_t i) {
-  const int64_t len = offsets[i + 1] - offsets[i];
+__device__ __forceinline__ int bucket_of(const Batch& b, int64_t i) {
+  const int64_t len = message_length(b, i);
   if (len <= 0) return 0;  // empty, or invalid (reported by the hash kernel)
   const int64_t p = (len + 31) >> 5;
   return p >= kBuckets ? kBuckets - 1 : static_cast<int>(p);
@@ -40,9 +41,9 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-__global__ void __launch_bounds__(kSortThreads) bucket_count_kernel(const int64_t* offsets,
-                                                                    uintptr_t base, int64_t n,
-                                                                    uint32_t* hist) {
+__global__ void __launch_bounds__(kSortThreads) bucket_count_kernel(Batch b, uint32_t* hist) {
+  resolve_count(b);
+  const int64_t n = b.n;
   __shared__ uint32_t h[kBuckets];
   for (int i = threadIdx.x; i < kBuckets; i += kSortThreads) h[i] = 0;
   __syncthreads();
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(kSortThreads) bucket_count_kernel(const int64_
 #pragma unroll
     for (int e = 0; e < kPerThread; ++e) {
       const int64_t i = c + e * kSortThreads + threadIdx.x;
-      const int key = i < n ? bucket_of(offsets, base, i) : -1;
+      const int key = i < n ? bucket_of(b, i) : -1;
       const unsigned peers = __match_any_sync(0xffffffffu, key);
       if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[key], __popc(peers));
     }
@@ -114,12 +115,12 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_
   if (tid == 0) *use_perm = any_long;
 }
 
-__global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(const int64_t* offsets,
-                                                                      uintptr_t byte_base, int64_t n,
-                                                                      uint32_t* cursor,
+__global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(Batch b, uint32_t* cursor,
                                                                       int32_t* perm,
                                                                       const int* use_perm) {
   if (*use_perm == 0) return;
+  resolve_count(b);
+  const int64_t n = b.n;
   __shared__ uint32_t cnt[kBuckets];
   __shared__ uint32_t base[kBuckets];
   const int lane = threadIdx.x & 31;
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(const int6
 #pragma unroll
     for (int e = 0; e < kPerThread; ++e) {
       const int64_t i = c + e * kSortThreads + threadIdx.x;
-      key[e] = i < n ? bucket_of(offsets, byte_base, i) : -1;
+      key[e] = i < n ? bucket_of(b, i) : -1;
       const unsigned peers = __match_any_sync(0xffffffffu, key[e]);
       const int leader = __ffs(peers) - 1;
       uint32_t first = 0;
@@ -155,20 +156,18 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(const int6
 
 }  // namespace
 
-cudaError_t launch_bucket_sort(const int64_t* offsets, const uint8_t* bytes, int64_t n,
-                               uint32_t* hist,
+cudaError_t launch_bucket_sort(const Batch& b, uint32_t* hist,
                                uint32_t* cursor, int32_t* perm, unsigned long long* next_tile,
                                int* use_perm, int num_sms, cudaStream_t stream, int* launches) {
+  const int64_t n = b.n;
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kBuckets, stream);
   if (e != cudaSuccess) return e;
   const int64_t chunks = (n + kChunk - 1) / kChunk;
   const int64_t cap = static_cast<int64_t>(num_sms) * 2;
   const int grid = static_cast<int>(chunks < cap ? chunks : cap);
-  const uintptr_t base = reinterpret_cast<uintptr_t>(bytes);
-  bucket_count_kernel<<<grid, kSortThreads, 0, stream>>>(offsets, base, n, hist);
+  bucket_count_kernel<<<grid, kSortThreads, 0, stream>>>(b, hist);
   bucket_scan_kernel<<<1, kSortThreads, 0, stream>>>(hist, cursor, next_tile, use_perm);
-  bucket_scatter_kernel<<<grid, kSortThreads, 0, stream>>>(offsets, base, n, cursor, perm,
-                                                           use_perm);
+  bucket_scatter_kernel<<<grid, kSortThreads, 0, stream>>>(b, cursor, perm, use_perm);
   *launches += 3;
   return cudaGetLastError();
 }

@@ -9,7 +9,8 @@ namespace hh {
 
 // Device error codes (same values as enum hh_status in include/hh.h).
 constexpr int kErrTimeout = 4;
-constexpr int kErrBadOffsets = 6;
+constexpr int kErrBadOffsets = 6;   // also: a segment outside the buffer
+constexpr int kErrBadKey = 8;       // a key index outside the key table
 
 // Length-sort buckets: bucket = min(ceil(len / 32), kBuckets - 1), the
 // number of Updates a message needs before finalisation, capped.
@@ -18,14 +19,20 @@ constexpr int kBuckets = 4096;
 // Messages per work tile of the staged kernel: one thread per message.
 constexpr int kTileRows = 128;
 
-// One batch, as every kernel sees it.
+// One batch, as every kernel sees it (hh_batch.cuh reads it).
 struct Batch {
   const uint8_t* bytes;      // message bytes
-  const int64_t* offsets;    // n + 1 offsets, or null for the fixed-length form
-  int64_t fixed_len;         // message length when offsets == null
-  const uint64_t* keys;      // 4 words (shared) or 4 * n words (per message)
+  const int64_t* offsets;    // n + 1 offsets (offsets form), or null
+  int64_t fixed_len;         // message length (fixed form: offsets and seg_start null)
+  const int64_t* seg_start;  // segments form: n starts, relative to bytes, or null
+  const int64_t* seg_len;    //                n lengths
+  int64_t bytes_len;         //                size of the bytes buffer
+  const uint64_t* keys;      // 4 words (shared), 4 * n (per message) or a key table
   int per_message_keys;
-  int64_t n;
+  const int32_t* key_index;  // n rows of the key table, or null
+  int32_t key_count;         // rows in the key table
+  int64_t n;                 // messages, or the capacity when n_dev is set
+  const int64_t* n_dev;      // device word with the message count (<= n), or null
   uint64_t* out;             // words * n
   int words;                 // 1, 2 or 4
   int* err;                  // device error word (first error wins)
@@ -84,9 +91,8 @@ cudaError_t launch_update_microbench(int variant, int64_t updates, int64_t threa
 // scatter does nothing: all-short batches keep index order, which keeps their
 // loads sequential.
 constexpr int kShortMax = 64;
-cudaError_t launch_bucket_sort(const int64_t* offsets, const uint8_t* bytes, int64_t n,
-                               uint32_t* hist,
-                               uint32_t* cursor, int32_t* perm, unsigned long long* next_tile,
-                               int* use_perm, int num_sms, cudaStream_t stream, int* launches);
+cudaError_t launch_bucket_sort(const Batch& b, uint32_t* hist, uint32_t* cursor, int32_t* perm,
+                               unsigned long long* next_tile, int* use_perm, int num_sms,
+                               cudaStream_t stream, int* launches);
 
 }  // namespace hh

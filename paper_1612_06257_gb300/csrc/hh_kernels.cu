@@ -22,6 +22,7 @@
 
 #include <cstdint>
 
+#include "hh_batch.cuh"
 #include "hh_device.cuh"
 #include "hh_internal.h"
 #include "hh_ptx.cuh"
@@ -31,22 +32,8 @@ namespace {
 
 // ------------------------------------------------------------ shared helpers
 
-__device__ __forceinline__ void message_bounds(const Batch& b, int64_t m, int64_t& start,
-                                               int64_t& len, bool& bad) {
-  if (b.offsets != nullptr) {
-    const int64_t s = b.offsets[m], e = b.offsets[m + 1];
-    bad = e < s;
-    start = s;
-    len = bad ? 0 : e - s;
-  } else {
-    start = m * b.fixed_len;
-    len = b.fixed_len;
-    bad = false;
-  }
-}
-
 __device__ __forceinline__ void load_key(const Batch& b, int64_t m, uint64_t key[4]) {
-  const uint64_t* k = b.per_message_keys ? b.keys + 4 * m : b.keys;
+  const uint64_t* k = key_of(b, m);
 #pragma unroll
   for (int i = 0; i < 4; ++i) key[i] = __ldg(k + i);
 }
@@ -76,12 +63,13 @@ __device__ __forceinline__ void load_packet_bytes(const uint8_t* p, uint32_t w[8
 // ----------------------------------------------------------------- naive path
 
 __global__ void __launch_bounds__(256) naive_kernel(Batch b) {
+  resolve_count(b);
   const int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (m >= b.n) return;
   int64_t start, len;
-  bool bad;
+  int bad;
   message_bounds(b, m, start, len, bad);
-  if (bad) record_error(b.err, kErrBadOffsets);
+  if (bad) record_error(b.err, bad);
   uint64_t key[4];
   load_key(b, m, key);
   State s;
@@ -156,6 +144,8 @@ __global__ void __launch_bounds__(kTileRows) staged_kernel(Batch b, Queue q) {
   __shared__ unsigned long long s_steps;
 
   const int t = threadIdx.x;
+  resolve_count(b);
+  const int64_t tiles = b.n_dev ? (b.n + kTileRows - 1) / kTileRows : q.tiles;
   if (t == 0) {
     for (int i = 0; i < NST; ++i) mbar_init(&bars[i], kTileRows);
     fence_mbar_init();
@@ -164,8 +154,8 @@ __global__ void __launch_bounds__(kTileRows) staged_kernel(Batch b, Queue q) {
 
   // Whole-batch byte range: bulk copies stay inside its 16-byte aligned part;
   // the (at most two) partial 16-byte blocks at its ends are read bytewise.
-  const int64_t lo = b.offsets ? b.offsets[0] : 0;
-  const int64_t hi = b.offsets ? b.offsets[b.n] : b.n * b.fixed_len;
+  int64_t lo, hi;
+  batch_range(b, lo, hi);
   const uintptr_t base = reinterpret_cast<uintptr_t>(b.bytes);
   const uintptr_t safe_lo = (base + lo + 15) & ~uintptr_t(15);
   const uintptr_t safe_hi = (base + hi) & ~uintptr_t(15);
@@ -185,17 +175,17 @@ __global__ void __launch_bounds__(kTileRows) staged_kernel(Batch b, Queue q) {
     __syncthreads();
     const int64_t tile = s_tile;
     static_tile += gridDim.x;
-    if (tile >= q.tiles) break;
+    if (tile >= tiles) break;
 
     const int64_t idx = tile * kTileRows + t;
     const bool valid = idx < b.n;
     int64_t m = 0, start = 0, len = 0;
-    bool bad = false;
+    int bad = 0;
     uint64_t key[4] = {0, 0, 0, 0};
     if (valid) {
       m = q.perm ? static_cast<int64_t>(q.perm[idx]) : idx;
       message_bounds(b, m, start, len, bad);
-      if (bad) record_error(b.err, kErrBadOffsets);
+      if (bad) record_error(b.err, bad);
       load_key(b, m, key);
     }
     const int64_t my_steps = (len + W - 1) / W;

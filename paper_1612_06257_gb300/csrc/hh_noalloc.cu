@@ -88,6 +88,7 @@ extern "C" int hh_hash_batch_noalloc(int bits, const uint64_t* keys, int key_mod
   b.bytes = bytes;
   b.offsets = offsets;
   b.fixed_len = 0;
+  b.seg_start = nullptr;
   b.keys = keys;
   b.per_message_keys = key_mode == HH_KEY_PER_MESSAGE;
   b.n = n;
@@ -98,7 +99,7 @@ extern "C" int hh_hash_batch_noalloc(int bits, const uint64_t* keys, int key_mod
   // The sort clears the bucket counts itself and its scan resets the queue
   // counter and the flag, so nothing left by an earlier call is read.
   int launches = 0;
-  cudaError_t e = hh::launch_bucket_sort(offsets, bytes, n, scr->hist, scr->cursor, scr->perm,
+  cudaError_t e = hh::launch_bucket_sort(b, scr->hist, scr->cursor, scr->perm,
                                          &scr->next_tile, &scr->use_perm, slot->num_sms, s,
                                          &launches);
   if (e != cudaSuccess) return HH_ERR_CUDA;

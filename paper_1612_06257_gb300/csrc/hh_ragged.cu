@@ -21,6 +21,7 @@
 
 #include <cstdint>
 
+#include "hh_batch.cuh"
 #include "hh_device.cuh"
 #include "hh_internal.h"
 #include "hh_ptx.cuh"
@@ -165,9 +166,11 @@ __global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* ring = smem + warp * L::kWarpBytes;
   const uint32_t ring_s = smem_u32(ring);
+  resolve_count(b);
+  const int64_t tiles = b.n_dev ? (b.n + 31) / 32 : q.tiles;
 
-  const int64_t lo = b.offsets ? b.offsets[0] : 0;
-  const int64_t hi = b.offsets ? b.offsets[b.n] : b.n * b.fixed_len;
+  int64_t lo, hi;
+  batch_range(b, lo, hi);
   const uintptr_t base = reinterpret_cast<uintptr_t>(b.bytes);
   const uintptr_t safe_lo = (base + lo + 15) & ~uintptr_t(15);
   const uintptr_t safe_hi = (base + hi) & ~uintptr_t(15);
@@ -191,26 +194,18 @@ __global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
       tile = static_tile;
       static_tile += static_step;
     }
-    if (tile >= q.tiles) break;
+    if (tile >= tiles) break;
 
     const int64_t idx = tile * 32 + lane;
     const bool valid = idx < b.n;
     int64_t m = 0, start = 0, len = 0;
-    bool bad = false;
+    int bad = 0;
     uint64_t key[4] = {0, 0, 0, 0};
     if (valid) {
       m = perm ? static_cast<int64_t>(perm[idx]) : idx;
-      if (b.offsets != nullptr) {
-        const int64_t s0 = b.offsets[m], e0 = b.offsets[m + 1];
-        bad = e0 < s0;
-        start = s0;
-        len = bad ? 0 : e0 - s0;
-        if (bad) record_error(b.err, kErrBadOffsets);
-      } else {
-        start = m * b.fixed_len;
-        len = b.fixed_len;
-      }
-      const uint64_t* kp = b.per_message_keys ? b.keys + 4 * m : b.keys;
+      message_bounds(b, m, start, len, bad);
+      if (bad) record_error(b.err, bad);
+      const uint64_t* kp = key_of(b, m);
 #pragma unroll
       for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
     }
@@ -333,23 +328,28 @@ __global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
 // no shared memory so that occupancy is set by registers alone.
 __global__ void __launch_bounds__(256) short_kernel(Batch b, const int* run_if) {
   if (run_if != nullptr && *run_if != 0) return;
-  const int64_t lo = b.offsets[0], hi = b.offsets[b.n];
+  resolve_count(b);
+  int64_t lo, hi;
+  batch_range(b, lo, hi);
   const uintptr_t base = reinterpret_cast<uintptr_t>(b.bytes);
   uint64_t key[4];
-  if (!b.per_message_keys) {
+  const bool shared_key = !b.per_message_keys && b.key_index == nullptr;
+  if (shared_key) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) key[i] = __ldg(b.keys + i);
   }
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; m < b.n;
        m += stride) {
-    const int64_t s0 = b.offsets[m], e0 = b.offsets[m + 1];
-    const bool bad = e0 < s0;
-    if (bad) record_error(b.err, kErrBadOffsets);
-    const int64_t len = bad ? 0 : (e0 - s0 < kShortMax ? e0 - s0 : kShortMax);
-    if (b.per_message_keys) {
+    int64_t s0, len;
+    int bad;
+    message_bounds(b, m, s0, len, bad);
+    if (bad) record_error(b.err, bad);
+    len = len < kShortMax ? len : kShortMax;
+    if (!shared_key) {
+      const uint64_t* kp = key_of(b, m);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) key[i] = __ldg(b.keys + 4 * m + i);
+      for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
     }
     State s;
     init(s, key);

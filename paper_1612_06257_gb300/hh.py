@@ -33,6 +33,7 @@ HH_ERR_TIMEOUT = 4
 HH_ERR_TOO_LARGE = 5
 HH_ERR_BAD_OFFSETS = 6
 HH_ERR_NO_DEVICE = 7
+HH_ERR_BAD_KEY_INDEX = 8
 
 HH_KEY_SHARED = 0
 HH_KEY_PER_MESSAGE = 1
@@ -48,7 +49,7 @@ EXPORTS = (
     "hh_init", "hh_destroy", "hh_reserve", "hh_hash64_batch", "hh_hash128_batch",
     "hh_hash256_batch", "hh_hash_fixed", "hh_hash_host", "hh_get_device_error",
     "hh_set_kernel", "hh_last_launch_count", "hh_status_string", "hh_set_staged_shape",
-    "hh_update_microbench", "hh_hash_batch_noalloc",
+    "hh_update_microbench", "hh_hash_batch_noalloc", "hh_hash_segments",
 )
 
 HH_REGIME_FIXED = 0
@@ -97,6 +98,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.hh_set_staged_shape.argtypes = [_vp, _int, _int, _int, _int]
         L.hh_update_microbench.argtypes = [_vp, _int, _i64, _i64, _vp, _vp]
         L.hh_hash_batch_noalloc.argtypes = [_int, _vp, _int, _vp, _vp, _i64, _vp, _vp, _vp]
+        L.hh_hash_segments.argtypes = [_vp, _int, _vp, ctypes.c_int32, _vp, _vp, _i64, _vp, _vp,
+                                       _i64, _vp, _vp, _vp]
         L.hh_status_string.argtypes = [_int]
         L.hh_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -206,6 +209,36 @@ def hh_hash_fixed(ctx, bits, keys, key_mode, data, msg_len, n, out=None, stream=
         _dev_ptr(data, "bytes", (torch.uint8,), dev), int(msg_len), int(n),
         _dev_ptr(out, "out", i64, dev), _stream_ptr(stream, dev))
     _check(st, "hh_hash_fixed")
+    return out
+
+
+def hh_hash_segments(ctx, bits, key_table, key_index, data, starts, lengths, out=None,
+                     stream=None, n_device=None):
+    """Hash segments data[starts[i] : starts[i] + lengths[i]] with key
+    key_table[key_index[i]] (key_index None: row 0 for all).  key_table: int64
+    [k, 4]; key_index: int32 [n]; starts, lengths: int64 [n]; all on the
+    context's device.  n_device: optional int64 [1] device tensor holding the
+    live message count (the arrays are then a capacity).  Returns out (int64
+    [n * bits // 64])."""
+    words = {64: 1, 128: 2, 256: 4}.get(int(bits))
+    if words is None:
+        raise ValueError("bits must be 64, 128 or 256")
+    n = starts.numel()
+    if lengths.numel() != n or (key_index is not None and key_index.numel() != n):
+        raise ValueError("starts, lengths and key_index must have n entries")
+    if out is None:
+        out = torch.empty(n * words, dtype=torch.int64, device=data.device)
+    dev = ctx.device
+    i64 = (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ())
+    st = load_library().hh_hash_segments(
+        ctx.ptr, int(bits), _dev_ptr(key_table, "key_table", i64, dev),
+        int(key_table.numel() // 4), _dev_ptr(key_index, "key_index", (torch.int32,), dev),
+        _dev_ptr(data, "bytes", (torch.uint8,), dev), int(data.numel()),
+        _dev_ptr(starts, "starts", (torch.int64,), dev),
+        _dev_ptr(lengths, "lengths", (torch.int64,), dev), n,
+        _dev_ptr(n_device, "n_device", (torch.int64,), dev),
+        _dev_ptr(out, "out", i64, dev), _stream_ptr(stream, dev))
+    _check(st, "hh_hash_segments")
     return out
 
 

@@ -8,6 +8,10 @@ hash's arithmetic; it only makes inputs, and both the CUDA path and the CPU
 checker read the same tensors.
 
 Workloads:
+  serving      requests of 1..4096 messages, each a segment of a device pool:
+               70% of lengths uniform in [0, 64], 25% exactly 1024, 5%
+               log-uniform in [1 MiB, 64 MiB] (file-like buffers); a random
+               256-bit key per request.
   fixed        n messages of exactly `length` bytes, contiguous, one key.
   ragged       lengths floor(exp(U(0, ln 65537))) - 1 in [0, 65536] (log-uniform),
                then forced to residue i mod 32 so every length mod 32 occurs;
@@ -132,3 +136,31 @@ def from_lengths(lengths, seed: int, device, per_message_keys: bool = True,
         mask = torch.repeat_interleave((~zero).to(torch.uint8), lengths)
         data *= mask
     return Workload("lengths", data, offsets, None, keys, per_message_keys, n)
+
+
+def serving_requests(count: int, pool_bytes: int, seed: int, max_messages: int = 4096,
+                     short_max: int = 64, kib: int = 1024, huge_min: int = 1 << 20,
+                     huge_max: int = 64 << 20, mix=(0.70, 0.25, 0.05)):
+    """Host-side request descriptors for the serving workload.
+
+    Returns a list of (key uint64[4], starts int64[m], lengths int64[m]) with
+    every segment inside [0, pool_bytes).  Start positions are uniform over
+    the pool, so requests read unrelated parts of it.
+    """
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        m = int(rng.integers(1, max_messages + 1))
+        kind = rng.choice(3, size=m, p=list(mix))
+        lengths = np.empty(m, dtype=np.int64)
+        n0, n1, n2 = (kind == 0).sum(), (kind == 1).sum(), (kind == 2).sum()
+        lengths[kind == 0] = rng.integers(0, short_max + 1, size=n0)
+        lengths[kind == 1] = kib
+        lengths[kind == 2] = np.floor(np.exp(rng.uniform(np.log(huge_min), np.log(huge_max),
+                                                         size=n2))).astype(np.int64)
+        lengths = np.minimum(lengths, pool_bytes)
+        starts = (rng.random(m) * (pool_bytes - lengths + 1)).astype(np.int64)
+        key = rng.integers(0, 2**64, size=4, dtype=np.uint64)
+        out.append((key, starts, lengths))
+    return out

@@ -60,3 +60,19 @@ def oracle_hashes(w, bits: int, indices=None, threads: int | None = None) -> np.
 
 def as_u64(t: torch.Tensor, words: int) -> np.ndarray:
     return t.cpu().numpy().view(np.uint64).reshape(-1, words)
+
+
+def oracle_segments(key_table, key_index, data, starts, lengths, bits: int) -> np.ndarray:
+    """Oracle hashes of segments (host numpy arrays): message i is
+    data[starts[i]:starts[i]+lengths[i]] keyed by key_table[key_index[i]]."""
+    n = starts.shape[0]
+    offs = np.zeros(n + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(lengths)
+    buf = np.zeros(int(offs[-1]), dtype=np.uint8)
+    for i in range(n):
+        buf[offs[i]:offs[i + 1]] = data[starts[i]:starts[i] + lengths[i]]
+    rows = np.zeros(n, dtype=np.int64) if key_index is None else key_index.astype(np.int64)
+    keys = np.ascontiguousarray(key_table.view(np.uint64).reshape(-1, 4)[rows])
+    out = np.zeros((n, bits // 64), dtype=np.uint64)
+    oracle.hash_batch(keys, True, buf, offs, bits, 0, n, out)
+    return out

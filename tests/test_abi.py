@@ -48,11 +48,11 @@ def test_library_exports_every_declared_symbol(lib):
 def test_status_strings(lib):
     from paper_1612_06257_gb300 import hh
     seen = set()
-    for code in range(0, 8):
+    for code in range(0, 9):
         s = hh.hh_status_string(code)
         assert s and s != "unknown status"
         seen.add(s)
-    assert len(seen) == 8
+    assert len(seen) == 9
     assert hh.hh_status_string(99) == "unknown status"
 
 
@@ -68,6 +68,8 @@ def test_null_context_is_rejected_without_cuda(lib):
     assert L.hh_destroy(None) == hh.HH_OK
     assert L.hh_last_launch_count(None) == 0
     assert L.hh_init(None, 0, None) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_hash_segments(None, 64, None, 1, None, None, 0, None, None, 1, None, None,
+                              None) == hh.HH_ERR_INVALID_ARG
 
 
 def test_init_without_a_gpu_reports_no_device(lib):

@@ -278,3 +278,59 @@ def test_full_size_short_64m_messages(ctx, bits):
     assert np.array_equal(got[idx], oracle_hashes(w, bits, indices=idx))
     del w
     torch.cuda.empty_cache()
+
+
+# ------------------------------------------------------------------ segments
+
+def _segments_case(n, seed, max_len, pool_bytes, key_rows):
+    g = torch.Generator().manual_seed(seed)
+    lengths = torch.randint(0, max_len + 1, (n,), generator=g, dtype=torch.int64)
+    starts = (torch.rand(n, generator=g, dtype=torch.float64) *
+              (pool_bytes - lengths).to(torch.float64)).to(torch.int64)
+    key_index = torch.randint(0, key_rows, (n,), generator=g, dtype=torch.int32)
+    gd = workloads.generator(seed, DEV)
+    pool = workloads.random_bytes(pool_bytes, gd, DEV)
+    table = workloads.random_u64((key_rows, 4), gd, DEV)
+    return table, key_index, pool, starts, lengths
+
+
+@pytest.mark.parametrize("kernel", ["auto", "unsorted", "naive"])
+@pytest.mark.parametrize("n,max_len", [(700, 3000), (5000, 64), (4000, 70000)])
+def test_segments_with_key_table(ctx, kernel, n, max_len):
+    """Segments of one pool in random order (overlapping), keys from a device
+    key table by index: the request-server batch form."""
+    from tests.helpers import oracle_segments
+    table, key_index, pool, starts, lengths = _segments_case(n, 40 + n, max_len, 1 << 22, 37)
+    hh.hh_set_kernel(ctx, KERNELS[kernel])
+    try:
+        out = hh.hh_hash_segments(ctx, 128, table, key_index.to(DEV), pool, starts.to(DEV),
+                                  lengths.to(DEV))
+        assert hh.hh_get_device_error(ctx) == hh.HH_OK
+    finally:
+        hh.hh_set_kernel(ctx, hh.HH_KERNEL_AUTO)
+    expect = oracle_segments(table.cpu().numpy(), key_index.numpy(), pool.cpu().numpy(),
+                             starts.numpy(), lengths.numpy(), 128)
+    assert np.array_equal(as_u64(out, 2), expect)
+
+
+def test_segments_shared_key_and_bad_descriptors(ctx):
+    from tests.helpers import oracle_segments
+    table, key_index, pool, starts, lengths = _segments_case(2000, 61, 200, 1 << 16, 1)
+    out = hh.hh_hash_segments(ctx, 64, table, None, pool, starts.to(DEV), lengths.to(DEV))
+    assert hh.hh_get_device_error(ctx) == hh.HH_OK
+    expect = oracle_segments(table.cpu().numpy(), None, pool.cpu().numpy(), starts.numpy(),
+                             lengths.numpy(), 64)
+    assert np.array_equal(as_u64(out, 1), expect)
+    # A segment past the end of the buffer, then a key index past the table.
+    bad = starts.clone()
+    bad[5] = (1 << 16) - 3
+    lengths2 = lengths.clone()
+    lengths2[5] = 10
+    out = hh.hh_hash_segments(ctx, 64, table, None, pool, bad.to(DEV), lengths2.to(DEV))
+    assert hh.hh_get_device_error(ctx) == hh.HH_ERR_BAD_OFFSETS
+    assert int(out[5].item()) == 0
+    kidx = torch.zeros(2000, dtype=torch.int32)
+    kidx[7] = 1
+    out = hh.hh_hash_segments(ctx, 64, table, kidx.to(DEV), pool, starts.to(DEV), lengths.to(DEV))
+    assert hh.hh_get_device_error(ctx) == hh.HH_ERR_BAD_KEY_INDEX
+    assert int(out[7].item()) == 0
