@@ -56,6 +56,7 @@ struct hh_ctx {
   int* d_err = nullptr;
   unsigned long long* d_next_tile = nullptr;
   int* d_use_perm = nullptr;
+  long long* d_huge = nullptr;
   uint32_t* d_hist = nullptr;
   uint32_t* d_cursor = nullptr;
   int32_t* d_perm = nullptr;
@@ -126,12 +127,13 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
     if (st != HH_OK) return st;
     int launches = 0;
     cudaError_t e = hh::launch_bucket_sort(b, ctx->d_hist, ctx->d_cursor, ctx->d_perm,
-                                           ctx->d_next_tile, ctx->d_use_perm, ctx->num_sms,
-                                           stream, &launches);
+                                           ctx->d_next_tile, ctx->d_use_perm, ctx->d_huge,
+                                           ctx->num_sms, stream, &launches);
     ctx->last_launches += launches;
     if (e != cudaSuccess) return to_status(e);
     q.perm = ctx->d_perm;
     q.use_perm = ctx->d_use_perm;
+    q.huge_count = ctx->d_huge;
     q.next_tile = ctx->d_next_tile;
   }
   cudaError_t e;
@@ -152,7 +154,9 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
       ctx->last_launches += 1;
       q.skip_if_short = 1;
     }
-    q.tiles = (n + 31) / 32;  // warp tiles
+    // The grid is sized for warp tiles of 32; pair tiles (16 messages) are
+    // taken from the same queue by the same persistent CTAs.
+    q.tiles = (n + 31) / 32;
     e = hh::launch_ragged(b, q, ctx->shape_ragged, ctx->num_sms, stream);
   }
   ctx->last_launches += 1;
@@ -236,6 +240,7 @@ int hh_init(hh_ctx** out, int device, const char* tune_cache_path) {
   bool ok = cudaMalloc(&ctx->d_err, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&ctx->d_next_tile, sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&ctx->d_use_perm, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&ctx->d_huge, sizeof(long long)) == cudaSuccess &&
             cudaMalloc(&ctx->d_hist, sizeof(uint32_t) * hh::kBuckets) == cudaSuccess &&
             cudaMalloc(&ctx->d_cursor, sizeof(uint32_t) * hh::kBuckets) == cudaSuccess &&
             cudaMemset(ctx->d_err, 0, sizeof(int)) == cudaSuccess &&
@@ -255,6 +260,7 @@ int hh_destroy(hh_ctx* ctx) {
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_next_tile);
   cudaFree(ctx->d_use_perm);
+  cudaFree(ctx->d_huge);
   cudaFree(ctx->d_hist);
   cudaFree(ctx->d_cursor);
   cudaFree(ctx->d_perm);

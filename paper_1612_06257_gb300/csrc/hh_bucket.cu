@@ -2,10 +2,13 @@
 //
 // A message of length L needs P = ceil(L / 32) Updates before finalisation
 // (one per whole 32-byte packet plus one for a partial packet, Sections 4.2
-// and 4.5).  Messages are counting-sorted by P, capped at kBuckets - 1, in
-// DESCENDING order, so that a warp tile holds messages of equal Update count
-// (no lane waits on another) and tiles are handed out longest first (the
-// long ones cannot end up last).
+// and 4.5).  Messages are counting-sorted by bucket(P) in DESCENDING order:
+// bucket = P below 2048 packets (64 KiB), then 128 buckets per doubling of P
+// (steps under 1%), up to messages of 4 GiB.  A warp tile thus holds
+// messages of (nearly) equal Update count, so no lane waits on another, and
+// tiles are handed out longest first, so the long ones cannot end up last.
+// The scan also counts the messages of kHugeBucket and above, which the hash
+// kernel runs two threads per message.
 //
 // Three kernels: per-block histograms merged with one global atomic per
 // non-empty bucket; a one-block exclusive scan in descending bucket order
@@ -31,8 +34,7 @@ constexpr int kChunk = kSortThreads * kPerThread;
 __device__ __forceinline__ int bucket_of(const Batch& b, int64_t i) {
   const int64_t len = message_length(b, i);
   if (len <= 0) return 0;  // empty, or invalid (reported by the hash kernel)
-  const int64_t p = (len + 31) >> 5;
-  return p >= kBuckets ? kBuckets - 1 : static_cast<int>(p);
+  return bucket_of_packets((len + 31) >> 5);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -67,7 +69,8 @@ __global__ void __launch_bounds__(kSortThreads) bucket_count_kernel(Batch b, uin
 __global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_t* hist,
                                                                    uint32_t* cursor,
                                                                    unsigned long long* next_tile,
-                                                                   int* use_perm) {
+                                                                   int* use_perm,
+                                                                   long long* huge_count) {
   constexpr int kPer = kBuckets / kSortThreads;  // 4 buckets per thread
   __shared__ uint32_t warp_sums[kSortThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -101,8 +104,12 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_
   uint32_t run = incl - local + (warp > 0 ? warp_sums[warp - 1] : 0u);
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
-    cursor[kBuckets - 1 - (tid * kPer + j)] = run;
+    const int bucket = kBuckets - 1 - (tid * kPer + j);
+    cursor[bucket] = run;
     run += v[j];
+    // Messages in buckets >= kHugeBucket: everything up to and including it
+    // in descending order.
+    if (bucket == kHugeBucket) *huge_count = static_cast<long long>(run);
   }
   if (tid == 0) *next_tile = 0ull;
   // Buckets above kShortMax / 32 hold messages longer than kShortMax bytes.
@@ -158,7 +165,8 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(Batch b, u
 
 cudaError_t launch_bucket_sort(const Batch& b, uint32_t* hist,
                                uint32_t* cursor, int32_t* perm, unsigned long long* next_tile,
-                               int* use_perm, int num_sms, cudaStream_t stream, int* launches) {
+                               int* use_perm, long long* huge_count, int num_sms,
+                               cudaStream_t stream, int* launches) {
   const int64_t n = b.n;
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kBuckets, stream);
   if (e != cudaSuccess) return e;
@@ -166,7 +174,8 @@ cudaError_t launch_bucket_sort(const Batch& b, uint32_t* hist,
   const int64_t cap = static_cast<int64_t>(num_sms) * 2;
   const int grid = static_cast<int>(chunks < cap ? chunks : cap);
   bucket_count_kernel<<<grid, kSortThreads, 0, stream>>>(b, hist);
-  bucket_scan_kernel<<<1, kSortThreads, 0, stream>>>(hist, cursor, next_tile, use_perm);
+  bucket_scan_kernel<<<1, kSortThreads, 0, stream>>>(hist, cursor, next_tile, use_perm,
+                                                      huge_count);
   bucket_scatter_kernel<<<grid, kSortThreads, 0, stream>>>(b, cursor, perm, use_perm);
   *launches += 3;
   return cudaGetLastError();

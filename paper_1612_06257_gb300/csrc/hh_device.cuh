@@ -213,6 +213,71 @@ __device__ __forceinline__ void remainder(State& s, uint32_t r, const uint32_t t
   update_words(s, pkt);
 }
 
+// ------------------------------------------------ one lane pair per thread
+// For very long messages two threads share one message: thread `half` keeps
+// lanes 2*half and 2*half+1 of every state vector.  Update mixes lanes only
+// within a pair (ZipperMerge, Section 4.1), so the packet loop needs no
+// exchange; the two threads trade v0 only in the finalisation Permute.
+struct Half {
+  uint64_t v0[2], v1[2], mul0[2], mul1[2];
+};
+
+__device__ __forceinline__ void init_half(Half& s, const uint64_t key[4], int half) {
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const uint64_t k = half ? key[2 + j] : key[j];  // no run-time array index
+    const uint64_t c0 = half ? init_lane(0, 2 + j) : init_lane(0, j);
+    const uint64_t c1 = half ? init_lane(1, 2 + j) : init_lane(1, j);
+    s.v0[j] = k ^ c0;
+    s.v1[j] = swap_halves(k) ^ c1;
+    s.mul0[j] = c0;
+    s.mul1[j] = c1;
+  }
+}
+
+// Update of one lane pair (the same statement order as update_v<1>).
+__device__ __forceinline__ void update_half(Half& s, uint64_t p0, uint64_t p1) {
+  const uint64_t p[2] = {p0, p1};
+  uint64_t add[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    s.v1[i] += p[i] + s.mul0[i];
+    s.mul0[i] ^= mul_lo(s.v1[i], s.v0[i] >> 32);
+    add[i] = s.mul1[i];
+    const uint32_t lo = lo32(s.v0[i]) + lo32(add[i]);  // lo(v0 + mul1)
+    s.mul1[i] ^= static_cast<uint64_t>(lo) * hi32(s.v1[i]);
+  }
+  uint64_t z[2];
+  zipper_pair(s.v1[0], s.v1[1], z[0], z[1]);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) s.v0[i] = s.v0[i] + add[i] + z[i];
+  zipper_pair(s.v0[0], s.v0[1], z[0], z[1]);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) s.v1[i] += z[i];
+}
+
+__device__ __forceinline__ void inject_size_half(Half& s, uint32_t r) {
+  const uint64_t inject = (static_cast<uint64_t>(r) << 32) + r;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    s.v0[i] += inject;
+    const uint32_t lo = lo32(s.v1[i]), hi = hi32(s.v1[i]);
+    s.v1[i] = join(__funnelshift_l(lo, lo, r), __funnelshift_l(hi, hi, r));
+  }
+}
+
+// Four rounds of Update(Permute(v0)) for a lane pair; all 32 lanes of the
+// warp must call it (partners are lanes l and l ^ 1).  Permute gives lane
+// pair (0,1) the rotated v0 lanes (2,3) and vice versa.
+__device__ __forceinline__ void finalize_half(Half& s) {
+#pragma unroll
+  for (int round = 0; round < 4; ++round) {
+    const uint64_t o0 = __shfl_xor_sync(0xffffffffu, s.v0[0], 1);
+    const uint64_t o1 = __shfl_xor_sync(0xffffffffu, s.v0[1], 1);
+    update_half(s, swap_halves(o0), swap_halves(o1));
+  }
+}
+
 // ---------------------------------------------------------------- Section 4.3
 // Four rounds of Update(Permute(v0)); Permute swaps v0's 128-bit halves and
 // the 32-bit halves of every lane (index map 2 3 0 1 6 7 4 5).

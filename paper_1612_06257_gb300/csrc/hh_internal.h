@@ -12,9 +12,20 @@ constexpr int kErrTimeout = 4;
 constexpr int kErrBadOffsets = 6;   // also: a segment outside the buffer
 constexpr int kErrBadKey = 8;       // a key index outside the key table
 
-// Length-sort buckets: bucket = min(ceil(len / 32), kBuckets - 1), the
-// number of Updates a message needs before finalisation, capped.
+// Length-sort buckets by the number of Updates P = ceil(len / 32) a message
+// needs before finalisation: P itself below 2048, then 128 buckets per
+// doubling of P (messages up to 4 GiB).  Messages in kHugeBucket and above
+// (P >= 4096, 128 KiB) run two threads per message.
 constexpr int kBuckets = 4096;
+constexpr int kHugeBucket = 2048 + 128;
+
+__host__ __device__ inline int bucket_of_packets(int64_t p) {
+  if (p < 2048) return static_cast<int>(p);
+  int lead = 11;  // index of p's leading bit (p >= 2^11)
+  while (lead < 62 && (p >> (lead + 1)) != 0) ++lead;
+  const int b = 2048 + 128 * (lead - 11) + static_cast<int>((p >> (lead - 7)) & 127);
+  return b < kBuckets ? b : kBuckets - 1;
+}
 
 // Messages per work tile of the staged kernel: one thread per message.
 constexpr int kTileRows = 128;
@@ -43,6 +54,7 @@ struct Queue {
   const int32_t* perm;       // processing order of messages, or null = 0..n-1
   const int* use_perm;       // device flag: 0 = ignore perm (no long message), or null
   int skip_if_short = 0;     // 1: return at once when *use_perm == 0 (the short kernel runs)
+  const long long* huge_count = nullptr;  // messages perm[0 .. *huge_count) run as pairs
   unsigned long long* next_tile;  // atomic tile counter (sorted order), or null = static
   int64_t tiles;
 };
@@ -92,7 +104,8 @@ cudaError_t launch_update_microbench(int variant, int64_t updates, int64_t threa
 // loads sequential.
 constexpr int kShortMax = 64;
 cudaError_t launch_bucket_sort(const Batch& b, uint32_t* hist, uint32_t* cursor, int32_t* perm,
-                               unsigned long long* next_tile, int* use_perm, int num_sms,
-                               cudaStream_t stream, int* launches);
+                               unsigned long long* next_tile, int* use_perm,
+                               long long* huge_count, int num_sms, cudaStream_t stream,
+                               int* launches);
 
 }  // namespace hh

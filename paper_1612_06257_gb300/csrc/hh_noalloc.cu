@@ -29,6 +29,7 @@ struct Scratch {
   uint32_t hist[hh::kBuckets];
   uint32_t cursor[hh::kBuckets];
   unsigned long long next_tile;
+  long long huge_count;
   int use_perm;
   int err;
 };
@@ -100,12 +101,13 @@ extern "C" int hh_hash_batch_noalloc(int bits, const uint64_t* keys, int key_mod
   // counter and the flag, so nothing left by an earlier call is read.
   int launches = 0;
   cudaError_t e = hh::launch_bucket_sort(b, scr->hist, scr->cursor, scr->perm,
-                                         &scr->next_tile, &scr->use_perm, slot->num_sms, s,
-                                         &launches);
+                                         &scr->next_tile, &scr->use_perm, &scr->huge_count,
+                                         slot->num_sms, s, &launches);
   if (e != cudaSuccess) return HH_ERR_CUDA;
   hh::Queue q{};
   q.perm = scr->perm;
   q.use_perm = &scr->use_perm;
+  q.huge_count = &scr->huge_count;
   q.next_tile = &scr->next_tile;
   q.tiles = (n + 31) / 32;
   e = hh::launch_ragged(b, q, hh::StagedShape{256, 2}, slot->num_sms, s);

@@ -159,6 +159,169 @@ __device__ __forceinline__ void hash_short(State& s, uintptr_t msg, uint32_t len
   }
 }
 
+// Half of a 32-byte packet: the 16 bytes at byte `off` of a row, as two
+// little-endian 64-bit lanes.
+template <bool kAligned>
+__device__ __forceinline__ void read_half_packet(const uint8_t* row, uint32_t off, uint64_t& p0,
+                                                 uint64_t& p1) {
+  if (kAligned) {
+    const uint4 a = lds128(row + off);
+    p0 = join(a.x, a.y);
+    p1 = join(a.z, a.w);
+  } else {
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(row + (off & ~3u));
+    const uint32_t sel = 0x3210u + 0x1111u * (off & 3u);
+    uint32_t x[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) x[i] = p[i];
+    p0 = join(__byte_perm(x[0], x[1], sel), __byte_perm(x[1], x[2], sel));
+    p1 = join(__byte_perm(x[2], x[3], sel), __byte_perm(x[3], x[4], sel));
+  }
+}
+
+// One pair tile: 16 messages of the huge prefix of the length order, two
+// lanes per message (lane 2s + h keeps lanes 2h, 2h+1 of message s's state).
+// Each message's row spans two ring rows and holds a 2W-byte window.
+template <int W, int NST>
+__device__ __forceinline__ void pair_tile(const Batch& b, const int32_t* perm, int64_t tile,
+                                          int64_t huge, uint8_t* ring, uint32_t ring_s,
+                                          uintptr_t base, uintptr_t safe_lo, uintptr_t safe_hi,
+                                          int lane) {
+  using L = RaggedLayout<W, NST>;
+  constexpr int WP = 2 * W;                   // window bytes per step
+  constexpr int kRowStride = 2 * L::kStride;  // one message row = two ring rows
+  constexpr int kChunks = WP / 16 + 1;
+  constexpr int kPerLane = (kChunks + 3) / 4;
+  const int slot = lane >> 1, half = lane & 1;
+  const int64_t idx = tile * 16 + slot;
+  const bool valid = idx < huge;
+  int64_t m = 0, start = 0, len = 0;
+  int bad = 0;
+  uint64_t key[4] = {0, 0, 0, 0};
+  if (valid) {
+    m = static_cast<int64_t>(perm[idx]);
+    message_bounds(b, m, start, len, bad);
+    if (bad && half == 0) record_error(b.err, bad);
+    const uint64_t* kp = key_of(b, m);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
+  }
+  Half s;
+  init_half(s, key, half);
+  const int64_t my_steps = (len + WP - 1) / WP;
+  const int64_t steps = warp_max(my_steps);
+  const uintptr_t msg = base + start;
+  const uint32_t mis = static_cast<uint32_t>(msg & 15);
+  const bool aligned = __all_sync(kFull, mis == 0 || !valid);
+  const int64_t packets = len >> 5;
+  const uint32_t r = static_cast<uint32_t>(len & 31);
+  const int64_t rem_step = r ? (packets * 32) / WP : -1;
+  const int part = lane & 3, slot_in_pass = lane >> 2;
+
+  auto issue = [&](int64_t k, int buf) {
+    uint8_t* stage = ring + buf * L::kStageBytes;
+    uintptr_t a0 = 0;
+    uint32_t range = 0;
+    if (half == 0 && k < my_steps) {
+      const uintptr_t gs = msg + static_cast<uintptr_t>(k) * WP;
+      const int64_t wend = k * WP + WP < len ? k * WP + WP : len;
+      const uintptr_t ge = msg + static_cast<uintptr_t>(wend);
+      a0 = gs & ~uintptr_t(15);
+      const uintptr_t a1 = (ge + 15) & ~uintptr_t(15);
+      const uintptr_t c0 = a0 > safe_lo ? a0 : safe_lo;
+      const uintptr_t c1 = a1 < safe_hi ? a1 : safe_hi;
+      uint32_t first = 0, end = 0;
+      if (c1 > c0) {
+        first = static_cast<uint32_t>((c0 - a0) >> 4);
+        end = static_cast<uint32_t>((c1 - a0) >> 4);
+      }
+      range = first | (end << 8);
+      if (c0 > gs || c1 < ge || c1 <= c0) {
+        uint8_t* row = stage + slot * kRowStride;
+        for (uintptr_t p = gs; p < ge; ++p)
+          if (p < c0 || p >= c1 || c1 <= c0) row[p - a0] = *reinterpret_cast<const uint8_t*>(p);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int row = 8 * h + slot_in_pass;
+      const uintptr_t rbase = static_cast<uintptr_t>(
+          __shfl_sync(kFull, static_cast<unsigned long long>(a0), 2 * row));
+      const uint32_t rr = __shfl_sync(kFull, range, 2 * row);
+      const uint32_t first = rr & 0xff, end = rr >> 8;
+      const char* src = reinterpret_cast<const char*>(rbase) + 16 * part;
+      const uint32_t dst = ring_s + buf * L::kStageBytes + row * kRowStride + 16 * part;
+#pragma unroll
+      for (int i = 0; i < kPerLane; ++i) {
+        const uint32_t c = part + 4 * i;
+        if (c >= first && c < end) cp_async16(dst + 64 * i, src + 64 * i);
+      }
+    }
+    cp_async_commit();
+  };
+
+  int buf_issue = 0, buf_read = 0;
+  for (int64_t k = 0; k < NST - 1; ++k) {
+    if (k < steps) issue(k, buf_issue);
+    else cp_async_commit();
+    buf_issue = (buf_issue + 1 == NST) ? 0 : buf_issue + 1;
+  }
+  for (int64_t k = 0; k < steps; ++k) {
+    if (k + NST - 1 < steps) issue(k + NST - 1, buf_issue);
+    else cp_async_commit();
+    buf_issue = (buf_issue + 1 == NST) ? 0 : buf_issue + 1;
+    cp_async_wait<NST - 1>();
+    __syncwarp();
+    if (k < my_steps) {
+      const uint8_t* row = ring + buf_read * L::kStageBytes + slot * kRowStride;
+      const int64_t p0 = k * (WP / 32);
+      const int64_t left = packets - p0;
+      const int count = left < WP / 32 ? static_cast<int>(left) : WP / 32;
+      if (aligned) {
+#pragma unroll 4
+        for (int j = 0; j < count; ++j) {
+          uint64_t x0, x1;
+          read_half_packet<true>(row, 32u * j + 16u * half, x0, x1);
+          update_half(s, x0, x1);
+        }
+      } else {
+#pragma unroll 4
+        for (int j = 0; j < count; ++j) {
+          uint64_t x0, x1;
+          read_half_packet<false>(row, mis + 32u * j + 16u * half, x0, x1);
+          update_half(s, x0, x1);
+        }
+      }
+      if (k == rem_step) {
+        uint32_t w[8], rp[8];
+        read_packet<false>(row, mis + static_cast<uint32_t>(packets * 32 - k * WP), w);
+        remainder_packet(r, w, rp);
+        inject_size_half(s, r);
+        if (half == 0) update_half(s, join(rp[0], rp[1]), join(rp[2], rp[3]));
+        else update_half(s, join(rp[4], rp[5]), join(rp[6], rp[7]));
+      }
+    }
+    __syncwarp();
+    buf_read = (buf_read + 1 == NST) ? 0 : buf_read + 1;
+  }
+  cp_async_wait<0>();
+  finalize_half(s);
+  if (valid) {
+    uint64_t h0 = s.v0[0] + s.v1[0] + s.mul0[0] + s.mul1[0];
+    uint64_t h1 = s.v0[1] + s.v1[1] + s.mul0[1] + s.mul1[1];
+    if (bad) h0 = h1 = 0;
+    uint64_t* o = b.out + m * b.words;
+    if (half == 0) {
+      o[0] = h0;
+      if (b.words >= 2) o[1] = h1;
+    } else if (b.words == 4) {
+      o[2] = h0;
+      o[3] = h1;
+    }
+  }
+  __syncwarp();
+}
+
 template <int W, int NST, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
   using L = RaggedLayout<W, NST>;
@@ -167,7 +330,6 @@ __global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
   uint8_t* ring = smem + warp * L::kWarpBytes;
   const uint32_t ring_s = smem_u32(ring);
   resolve_count(b);
-  const int64_t tiles = b.n_dev ? (b.n + 31) / 32 : q.tiles;
 
   int64_t lo, hi;
   batch_range(b, lo, hi);
@@ -181,6 +343,11 @@ __global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
 
   if (q.skip_if_short && q.use_perm != nullptr && *q.use_perm == 0) return;  // short kernel runs
   const int32_t* perm = (q.perm && (q.use_perm == nullptr || *q.use_perm)) ? q.perm : nullptr;
+  // Tiles: first the pair tiles of the huge prefix of the length order (16
+  // messages each), then warp tiles of 32 messages.
+  const int64_t huge = (perm != nullptr && q.huge_count != nullptr) ? *q.huge_count : 0;
+  const int64_t huge_tiles = (huge + 15) / 16;
+  const int64_t tiles = huge_tiles + (b.n - huge + 31) / 32;
   int64_t static_tile = static_cast<int64_t>(blockIdx.x) * WARPS + warp;
   const int64_t static_step = static_cast<int64_t>(gridDim.x) * WARPS;
 
@@ -195,8 +362,12 @@ __global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
       static_tile += static_step;
     }
     if (tile >= tiles) break;
+    if (tile < huge_tiles) {
+      pair_tile<W, NST>(b, perm, tile, huge, ring, ring_s, base, safe_lo, safe_hi, lane);
+      continue;
+    }
 
-    const int64_t idx = tile * 32 + lane;
+    const int64_t idx = huge + (tile - huge_tiles) * 32 + lane;
     const bool valid = idx < b.n;
     int64_t m = 0, start = 0, len = 0;
     int bad = 0;

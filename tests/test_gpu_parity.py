@@ -334,3 +334,22 @@ def test_segments_shared_key_and_bad_descriptors(ctx):
     out = hh.hh_hash_segments(ctx, 64, table, kidx.to(DEV), pool, starts.to(DEV), lengths.to(DEV))
     assert hh.hh_get_device_error(ctx) == hh.HH_ERR_BAD_KEY_INDEX
     assert int(out[7].item()) == 0
+
+
+def test_huge_messages_run_in_thread_pairs(ctx):
+    """Messages of 128 KiB and more take the two-threads-per-message tiles at
+    the head of the length order; mixed with ordinary and short ones, with
+    unaligned starts, every width, against the oracle."""
+    g = torch.Generator().manual_seed(91)
+    lengths = torch.cat([
+        (torch.rand(40, generator=g, dtype=torch.float64) * (4 << 20 - 1)).to(torch.int64) + (1 << 17),
+        torch.full((3,), 1 << 17), torch.full((2,), (1 << 17) - 1),
+        torch.randint(0, 5000, (1500,), generator=g)])
+    lengths = lengths[torch.randperm(lengths.numel(), generator=g)]
+    w = workloads.from_lengths(lengths, seed=91, device=DEV, per_message_keys=True)
+    for bits in (64, 128, 256):
+        got = run_ragged(ctx, w, bits)
+        big = np.nonzero(lengths.numpy() >= (1 << 17))[0]
+        idx = np.unique(np.concatenate([big, np.arange(0, w.n, 7)]))
+        assert np.array_equal(got[idx], oracle_hashes(w, bits, indices=idx)), bits
+        assert np.array_equal(got, run_ragged(ctx, w, bits, "unsorted"))
