@@ -6,6 +6,7 @@ uniform random bytes (1 GiB) with one 256-bit key, through libhh's C ABI.
 The inputs (1 GiB) are larger than L2 (129 MB), so no flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload small|ragged|short|serving
 
 Rank 0 prints one JSON line.  --impl reference times the CPU oracle (the
 scalar C implementation the tests check against) on the host cores instead.
@@ -44,6 +45,10 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default=None,
+                   choices=["small", "ragged", "short", "serving"],
+                   help="measure another batch shape instead (one JSON line; not the "
+                        "headline step)")
     return p.parse_args()
 
 
@@ -394,7 +399,10 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
+    if args.workload is not None:
+        from paper_1612_06257_gb300 import bench_workloads
+        res = bench_workloads.run(args.workload) if rank == 0 else None
+    elif args.impl == "reference":
         res = run_reference(args, rank, world)
     else:
         res = run_ours(args, rank, world, local_rank)

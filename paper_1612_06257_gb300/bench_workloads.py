@@ -1,0 +1,172 @@
+"""Measurements of the other batch shapes (bench.py --workload NAME).
+
+  small    4096 messages x 1024 B, one key: microseconds per batch with the
+           inputs hot in L2 and with L2 flushed between batches.
+  ragged   2^22 messages, lengths log-uniform in [0, 65536], per-message
+           keys (about 25 GB): GB/s against the HBM peak.
+  short    2^26 messages of 0..64 B (10% all zero), one key: hashes/s for
+           64- and 128-bit output against the integer ceiling that the
+           Update microbenchmark measures in the same run.
+  serving  the request mix (70% <= 64 B, 25% 1 KiB, 5% 1-64 MiB buffers,
+           1..4096 messages and one key per request) through the
+           continuous-batching server: saturation GB/s, then p50/p99
+           latency at Poisson arrival rates swept over 0.1-0.9 of it.
+
+Every input is synthetic and seeded; each workload prints one JSON line.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import numpy as np
+import torch
+
+from paper_1612_06257_gb300 import hh, serve, workloads
+
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peak_hbm():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    try:
+        with open(os.path.join(root, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _time(fn, reps, flush=None):
+    fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return float(np.median(times)), times
+
+
+def small(ctx, dev):
+    w = workloads.fixed(4096, 1024, seed=1, device=dev)
+    out = torch.empty(w.n, dtype=torch.int64, device=dev)
+    junk = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    fn = lambda: hh.hh_hash_fixed(ctx, 64, w.keys, 0, w.data, 1024, w.n, out=out)  # noqa: E731
+    # Hot: 200 back-to-back launches (inputs stay in L2); cold: one launch
+    # after writing a 512 MiB buffer, each timed alone.
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record()
+    for _ in range(200):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    hot = e0.elapsed_time(e1) / 200
+    cold, _ = _time(fn, 50, flush=lambda: junk.fill_(1))
+    return {"workload": "4096 x 1024 B, one key, 64-bit (fixed-length batch)",
+            "us_per_batch_hot_l2": round(hot * 1e3, 2), "us_per_batch_cold_l2": round(cold * 1e3, 2),
+            "gbps_hot": round(w.total_bytes / hot / 1e6, 1),
+            "gbps_cold": round(w.total_bytes / cold / 1e6, 1),
+            "note": "4 MiB fits L2 and 4096 threads fill 27 of 152 SMs: a latency regime"}
+
+
+def ragged(ctx, dev):
+    w = workloads.ragged(1 << 22, seed=2, device=dev)
+    out = torch.empty(w.n, dtype=torch.int64, device=dev)
+    fn = lambda: hh.hh_hash64_batch(ctx, w.keys, 1, w.data, w.offsets, out=out)  # noqa: E731
+    ms, _ = _time(fn, 10)
+    launches = hh.hh_last_launch_count(ctx)
+    alg = w.total_bytes + 8 * (w.n + 1) + 32 * w.n + 8 * w.n
+    peak, kind = _peak_hbm()
+    return {"workload": "2^22 messages, log-uniform lengths in [0, 65536], per-message keys, "
+                        "64-bit", "bytes": w.total_bytes, "ms_per_batch": round(ms, 3),
+            "gbps": round(w.total_bytes / ms / 1e6, 1), "hashes_per_s": round(w.n / ms * 1e3, 1),
+            "roofline": {"bound": "hbm", "achieved": round(alg / ms / 1e6, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(alg / ms / 1e6 / peak, 4),
+                         "peak_source": kind, "algorithmic_bytes": alg},
+            "launches_per_batch": launches}
+
+
+def _update_ceiling(ctx, dev):
+    """Updates per second of the integer-issue microbenchmark (no memory)."""
+    threads, updates = 152 * 1024 * 4, 1024
+    out = hh.hh_update_microbench(ctx, 1, updates, threads)
+    ms, _ = _time(lambda: hh.hh_update_microbench(ctx, 1, updates, threads, out=out), 5)
+    return threads * updates / (ms / 1e3)
+
+
+def short(ctx, dev):
+    w = workloads.short(1 << 26, seed=3, device=dev)
+    lengths = (w.offsets[1:] - w.offsets[:-1]).cpu().numpy()
+    upd_per_hash = float(np.mean(lengths // 32 + (lengths % 32 != 0) + 4))
+    ceiling = _update_ceiling(ctx, dev) / upd_per_hash
+    res = {"workload": "2^26 messages of 0..64 B (10% all zero), one key",
+           "updates_per_hash": round(upd_per_hash, 3),
+           "integer_ceiling_hashes_per_s": round(ceiling, 1)}
+    for bits, fn in ((64, hh.hh_hash64_batch), (128, hh.hh_hash128_batch)):
+        out = torch.empty(w.n * bits // 64, dtype=torch.int64, device=dev)
+        ms, _ = _time(lambda: fn(ctx, w.keys, 0, w.data, w.offsets, out=out), 10)
+        hps = w.n / (ms / 1e3)
+        res["hashes_per_s_%d" % bits] = round(hps, 1)
+        res["integer_frac_%d" % bits] = round(hps / ceiling, 4)
+        res["gbps_%d" % bits] = round(w.total_bytes / ms / 1e6, 1)
+    return res
+
+
+def serving(ctx, dev, requests=64, pool_gib=8, rates=(0.1, 0.3, 0.5, 0.7, 0.9)):
+    pool = workloads.random_bytes(pool_gib << 30, workloads.generator(7, dev), dev)
+    specs = workloads.serving_requests(requests, pool.numel(), seed=8)
+
+    def fresh():
+        return [serve.Request(key=k, starts=s, lengths=l, rid=i) for i, (k, s, l) in enumerate(specs)]
+
+    server = serve.HashServer(pool, bits=64, slots=16, capacity=1 << 16, max_requests_per_batch=4,
+                              max_bytes_in_flight=96 << 30, use_graphs=True)
+    try:
+        warm = fresh()[:4]
+        for r in warm:
+            server.submit(r)
+        server.drain()
+        sat = serve.run_poisson(server, fresh(), rate_per_s=1e9, seed=1)
+        sat_rate = sat["requests"] / sat["wall_s"]
+        sweep = []
+        for f in rates:
+            st = serve.run_poisson(server, fresh(), rate_per_s=f * sat_rate, seed=2)
+            sweep.append({"load": f, "rate_per_s": round(st["rate_per_s"], 2),
+                          "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
+                          "gbps": round(st["gbps"], 1)})
+        errors = server.device_errors()
+    finally:
+        server.close()
+    total = sum(int(l.sum()) for _, _, l in specs)
+    return {"workload": "serving mix: %d requests (1-4096 messages; 70%% <= 64 B, 25%% 1 KiB, "
+                        "5%% 1-64 MiB), per-request keys, 16 stream slots with CUDA graphs "
+                        "(<= 4 requests per batch), 96 GiB in-flight cap" % requests,
+            "bytes_per_pass": total,
+            "saturation": {"gbps": round(sat["gbps"], 1), "requests_per_s": round(sat_rate, 2),
+                           "p50_ms": round(sat["p50_ms"], 2), "p99_ms": round(sat["p99_ms"], 2)},
+            "sweep": sweep, "device_errors": errors}
+
+
+WORKLOADS = {"small": small, "ragged": ragged, "short": short, "serving": serving}
+
+
+def run(name: str) -> dict:
+    from paper_1612_06257_gb300 import build
+    build.build()
+    dev = "cuda:0"
+    ctx = hh.hh_init(0)
+    try:
+        res = WORKLOADS[name](ctx, dev)
+    finally:
+        hh.hh_destroy(ctx)
+    res["name"] = name
+    res["data"] = "synthetic (seeded, generated on device)"
+    return res
