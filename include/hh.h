@@ -82,8 +82,9 @@ enum hh_kernel {
 /*
  * Create a context on CUDA device `device`.  It owns a small device error
  * word, a work-queue counter and scratch memory for the length sort, which
- * grows when a call needs more (see hh_reserve).  `tune_cache_path` is
- * reserved for a tuning table and must be NULL.
+ * grows when a call needs more (see hh_reserve).  `tune_cache_path` names a
+ * tuning table written by hh_tune_save (HH_ERR_INVALID_ARG if it cannot be
+ * read), or NULL for the built-in choices measured on GB300.
  * Returns HH_ERR_NO_DEVICE when the device is absent or not sm_103a.
  * The caller's current device is restored before returning.
  */
@@ -243,6 +244,27 @@ int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages,
 #define HH_UPDATE_VARIANTS 5
 int hh_update_microbench(hh_ctx* ctx, int variant, int64_t updates, int64_t threads,
                          uint64_t* out, void* stream);
+
+/*
+ * Autotuner (no counterpart in the paper).  Times the candidate kernel
+ * shapes on synthetic batches of at most `max_device_bytes` (>= 64 MiB; it
+ * allocates that much plus small buffers, and frees them before returning)
+ * and keeps, in ctx, the fastest per length regime: for fixed-length
+ * batches per length class (<= 64, <= 256, <= 1024, <= 8192 bytes, larger)
+ * the TMA kernel's window, pipeline depth and messages per thread; for
+ * ragged batches the warp-tile kernel's window and depth; and the message
+ * length above which a message runs two threads per message (or never).
+ * Synchronous; takes seconds.  Results are identical whatever is chosen.
+ */
+int hh_autotune(hh_ctx* ctx, int64_t max_device_bytes);
+
+/* Write ctx's tuning table as text (hh_init reads it back). */
+int hh_tune_save(hh_ctx* ctx, const char* path);
+
+/* The tuning table as text into buf (NUL-terminated), followed, after an
+ * hh_autotune, by comment lines ('#') with each candidate's measured time;
+ * HH_ERR_TOO_LARGE if buf_len is too small (8 KiB always suffices). */
+int hh_tune_describe(hh_ctx* ctx, char* buf, int64_t buf_len);
 
 /* Number of kernel launches the last hash call on ctx enqueued. */
 int hh_last_launch_count(hh_ctx* ctx);

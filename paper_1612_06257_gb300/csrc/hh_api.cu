@@ -11,6 +11,7 @@
 #include <new>
 
 #include "hh.h"
+#include "hh_context.h"
 #include "hh_internal.h"
 
 namespace {
@@ -32,45 +33,6 @@ struct DeviceGuard {
     if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
   }
 };
-
-struct HostSlot {
-  uint8_t* bytes = nullptr;
-  size_t bytes_cap = 0;
-  int64_t* offsets = nullptr;
-  size_t offsets_cap = 0;  // elements
-  uint64_t* keys = nullptr;
-  size_t keys_cap = 0;     // elements
-  uint64_t* out = nullptr;
-  size_t out_cap = 0;      // elements
-  cudaEvent_t staged = nullptr;  // inputs on the device
-  cudaEvent_t hashed = nullptr;  // kernel done
-  cudaEvent_t drained = nullptr; // output copied back: slot reusable
-};
-
-}  // namespace
-
-struct hh_ctx {
-  int device = 0;
-  int num_sms = 0;
-  int kernel = HH_KERNEL_AUTO;
-  int* d_err = nullptr;
-  unsigned long long* d_next_tile = nullptr;
-  int* d_use_perm = nullptr;
-  long long* d_huge = nullptr;
-  uint32_t* d_hist = nullptr;
-  uint32_t* d_cursor = nullptr;
-  int32_t* d_perm = nullptr;
-  int64_t perm_cap = 0;
-  hh::StagedShape shape_ragged{256, 2};  // warp-tile kernel
-  hh::StagedShape shape_fixed{128, 2, 2};  // the TMA kernel's shape
-  hh::StagedShape shape_bulk{256, 2};    // per-thread bulk-copy kernel
-  int last_launches = 0;
-  // Host-buffer path.
-  cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
-  HostSlot slots[2];
-};
-
-namespace {
 
 int to_status(cudaError_t e) {
   if (e == cudaSuccess) return HH_OK;
@@ -116,7 +78,8 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
   }
   if (fixed && b.key_index == nullptr && hh::fixed_tma_supported(b.bytes, b.fixed_len, n)) {
     ctx->last_launches = 1;
-    return to_status(hh::launch_fixed_tma(b, ctx->shape_fixed, ctx->num_sms, stream));
+    return to_status(hh::launch_fixed_tma(b, ctx->tune.fixed[hh::fixed_class(b.fixed_len)],
+                                          ctx->num_sms, stream));
   }
 
   const bool sort = !fixed && ctx->kernel != HH_KERNEL_STAGED_UNSORTED && n >= kSortMinMessages;
@@ -128,7 +91,7 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
     int launches = 0;
     cudaError_t e = hh::launch_bucket_sort(b, ctx->d_hist, ctx->d_cursor, ctx->d_perm,
                                            ctx->d_next_tile, ctx->d_use_perm, ctx->d_huge,
-                                           ctx->num_sms, stream, &launches);
+                                           ctx->tune.huge_bucket, ctx->num_sms, stream, &launches);
     ctx->last_launches += launches;
     if (e != cudaSuccess) return to_status(e);
     q.perm = ctx->d_perm;
@@ -157,7 +120,7 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
     // The grid is sized for warp tiles of 32; pair tiles (16 messages) are
     // taken from the same queue by the same persistent CTAs.
     q.tiles = (n + 31) / 32;
-    e = hh::launch_ragged(b, q, ctx->shape_ragged, ctx->num_sms, stream);
+    e = hh::launch_ragged(b, q, ctx->tune.ragged, ctx->num_sms, stream);
   }
   ctx->last_launches += 1;
   return to_status(e);
@@ -222,7 +185,6 @@ const char* hh_status_string(int status) {
 }
 
 int hh_init(hh_ctx** out, int device, const char* tune_cache_path) {
-  (void)tune_cache_path;
   if (out == nullptr) return HH_ERR_INVALID_ARG;
   *out = nullptr;
   int count = 0;
@@ -237,6 +199,10 @@ int hh_init(hh_ctx** out, int device, const char* tune_cache_path) {
   if (ctx == nullptr) return HH_ERR_NO_MEMORY;
   ctx->device = device;
   ctx->num_sms = prop.multiProcessorCount;
+  if (tune_cache_path != nullptr && !hh::load_tune_table(tune_cache_path, ctx->tune)) {
+    delete ctx;
+    return HH_ERR_INVALID_ARG;
+  }
   bool ok = cudaMalloc(&ctx->d_err, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&ctx->d_next_tile, sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&ctx->d_use_perm, sizeof(int)) == cudaSuccess &&
@@ -264,7 +230,7 @@ int hh_destroy(hh_ctx* ctx) {
   cudaFree(ctx->d_hist);
   cudaFree(ctx->d_cursor);
   cudaFree(ctx->d_perm);
-  for (HostSlot& s : ctx->slots) {
+  for (hh::HostSlot& s : ctx->slots) {
     cudaFree(s.bytes);
     cudaFree(s.offsets);
     cudaFree(s.keys);
@@ -362,7 +328,7 @@ int hh_hash_host(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
         cudaStreamCreateWithFlags(&ctx->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->s_d2h, cudaStreamNonBlocking) != cudaSuccess)
       return HH_ERR_CUDA;
-    for (HostSlot& s : ctx->slots) {
+    for (hh::HostSlot& s : ctx->slots) {
       if (cudaEventCreateWithFlags(&s.staged, cudaEventDisableTiming) != cudaSuccess ||
           cudaEventCreateWithFlags(&s.hashed, cudaEventDisableTiming) != cudaSuccess ||
           cudaEventCreateWithFlags(&s.drained, cudaEventDisableTiming) != cudaSuccess)
@@ -388,7 +354,7 @@ int hh_hash_host(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
       m1 = lo;
     }
     if (offsets[m1] < offsets[m0]) return HH_ERR_BAD_OFFSETS;
-    HostSlot& s = ctx->slots[chunk_index & 1];
+    hh::HostSlot& s = ctx->slots[chunk_index & 1];
     const int64_t cn = m1 - m0;
     const size_t cbytes = static_cast<size_t>(offsets[m1] - offsets[m0]);
     // The slot's previous chunk must have drained before its buffers change.
@@ -489,10 +455,10 @@ int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages,
   const hh::StagedShape shape{window, stages, messages_per_thread};
   if (regime == HH_REGIME_FIXED) {
     if (!hh::fixed_shape_valid(shape)) return HH_ERR_INVALID_ARG;
-    ctx->shape_fixed = shape;
+    for (hh::StagedShape& f : ctx->tune.fixed) f = shape;  // every length class
   } else if (regime == HH_REGIME_RAGGED) {
     if (!hh::ragged_shape_valid(shape)) return HH_ERR_INVALID_ARG;
-    ctx->shape_ragged = shape;
+    ctx->tune.ragged = shape;
   } else {
     if (hh::staged_smem_bytes(shape) == 0) return HH_ERR_INVALID_ARG;
     ctx->shape_bulk = shape;

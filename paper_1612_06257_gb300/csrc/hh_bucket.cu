@@ -7,8 +7,8 @@
 // (steps under 1%), up to messages of 4 GiB.  A warp tile thus holds
 // messages of (nearly) equal Update count, so no lane waits on another, and
 // tiles are handed out longest first, so the long ones cannot end up last.
-// The scan also counts the messages of kHugeBucket and above, which the hash
-// kernel runs two threads per message.
+// The scan also counts the messages of a given bucket and above (by default
+// kHugeBucket, 128 KiB), which the hash kernel runs two threads per message.
 //
 // Three kernels: per-block histograms merged with one global atomic per
 // non-empty bucket; a one-block exclusive scan in descending bucket order
@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_
                                                                    uint32_t* cursor,
                                                                    unsigned long long* next_tile,
                                                                    int* use_perm,
-                                                                   long long* huge_count) {
+                                                                   long long* huge_count,
+                                                                   int huge_bucket) {
   constexpr int kPer = kBuckets / kSortThreads;  // 4 buckets per thread
   __shared__ uint32_t warp_sums[kSortThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -107,11 +108,14 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_
     const int bucket = kBuckets - 1 - (tid * kPer + j);
     cursor[bucket] = run;
     run += v[j];
-    // Messages in buckets >= kHugeBucket: everything up to and including it
+    // Messages in buckets >= huge_bucket: everything up to and including it
     // in descending order.
-    if (bucket == kHugeBucket) *huge_count = static_cast<long long>(run);
+    if (bucket == huge_bucket) *huge_count = static_cast<long long>(run);
   }
-  if (tid == 0) *next_tile = 0ull;
+  if (tid == 0) {
+    *next_tile = 0ull;
+    if (huge_bucket >= kBuckets) *huge_count = 0;  // pair tiles switched off
+  }
   // Buckets above kShortMax / 32 hold messages longer than kShortMax bytes.
   const int long_bucket = kShortMax / 32 + 1;
   bool mine = false;
@@ -165,8 +169,8 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(Batch b, u
 
 cudaError_t launch_bucket_sort(const Batch& b, uint32_t* hist,
                                uint32_t* cursor, int32_t* perm, unsigned long long* next_tile,
-                               int* use_perm, long long* huge_count, int num_sms,
-                               cudaStream_t stream, int* launches) {
+                               int* use_perm, long long* huge_count, int huge_bucket,
+                               int num_sms, cudaStream_t stream, int* launches) {
   const int64_t n = b.n;
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kBuckets, stream);
   if (e != cudaSuccess) return e;
@@ -175,7 +179,7 @@ cudaError_t launch_bucket_sort(const Batch& b, uint32_t* hist,
   const int grid = static_cast<int>(chunks < cap ? chunks : cap);
   bucket_count_kernel<<<grid, kSortThreads, 0, stream>>>(b, hist);
   bucket_scan_kernel<<<1, kSortThreads, 0, stream>>>(hist, cursor, next_tile, use_perm,
-                                                      huge_count);
+                                                      huge_count, huge_bucket);
   bucket_scatter_kernel<<<grid, kSortThreads, 0, stream>>>(b, cursor, perm, use_perm);
   *launches += 3;
   return cudaGetLastError();

@@ -14,8 +14,9 @@ constexpr int kErrBadKey = 8;       // a key index outside the key table
 
 // Length-sort buckets by the number of Updates P = ceil(len / 32) a message
 // needs before finalisation: P itself below 2048, then 128 buckets per
-// doubling of P (messages up to 4 GiB).  Messages in kHugeBucket and above
-// (P >= 4096, 128 KiB) run two threads per message.
+// doubling of P (messages up to 4 GiB).  By default messages in kHugeBucket
+// and above (P >= 4096, 128 KiB) run two threads per message; the autotuner
+// may raise that threshold or switch pairs off.
 constexpr int kBuckets = 4096;
 constexpr int kHugeBucket = 2048 + 128;
 
@@ -105,7 +106,7 @@ cudaError_t launch_update_microbench(int variant, int64_t updates, int64_t threa
 constexpr int kShortMax = 64;
 cudaError_t launch_bucket_sort(const Batch& b, uint32_t* hist, uint32_t* cursor, int32_t* perm,
                                unsigned long long* next_tile, int* use_perm,
-                               long long* huge_count, int num_sms, cudaStream_t stream,
-                               int* launches);
+                               long long* huge_count, int huge_bucket, int num_sms,
+                               cudaStream_t stream, int* launches);
 
 }  // namespace hh

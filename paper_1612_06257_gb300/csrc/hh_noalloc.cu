@@ -102,7 +102,7 @@ extern "C" int hh_hash_batch_noalloc(int bits, const uint64_t* keys, int key_mod
   int launches = 0;
   cudaError_t e = hh::launch_bucket_sort(b, scr->hist, scr->cursor, scr->perm,
                                          &scr->next_tile, &scr->use_perm, &scr->huge_count,
-                                         slot->num_sms, s, &launches);
+                                         hh::kHugeBucket, slot->num_sms, s, &launches);
   if (e != cudaSuccess) return HH_ERR_CUDA;
   hh::Queue q{};
   q.perm = scr->perm;

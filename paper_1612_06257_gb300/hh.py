@@ -49,7 +49,8 @@ EXPORTS = (
     "hh_init", "hh_destroy", "hh_reserve", "hh_hash64_batch", "hh_hash128_batch",
     "hh_hash256_batch", "hh_hash_fixed", "hh_hash_host", "hh_get_device_error",
     "hh_set_kernel", "hh_last_launch_count", "hh_status_string", "hh_set_staged_shape",
-    "hh_update_microbench", "hh_hash_batch_noalloc", "hh_hash_segments",
+    "hh_update_microbench", "hh_hash_batch_noalloc", "hh_hash_segments", "hh_autotune",
+    "hh_tune_save", "hh_tune_describe",
 )
 
 HH_REGIME_FIXED = 0
@@ -98,6 +99,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.hh_set_staged_shape.argtypes = [_vp, _int, _int, _int, _int]
         L.hh_update_microbench.argtypes = [_vp, _int, _i64, _i64, _vp, _vp]
         L.hh_hash_batch_noalloc.argtypes = [_int, _vp, _int, _vp, _vp, _i64, _vp, _vp, _vp]
+        L.hh_autotune.argtypes = [_vp, _i64]
+        L.hh_tune_save.argtypes = [_vp, ctypes.c_char_p]
+        L.hh_tune_describe.argtypes = [_vp, ctypes.c_char_p, _i64]
         L.hh_hash_segments.argtypes = [_vp, _int, _vp, ctypes.c_int32, _vp, _vp, _i64, _vp, _vp,
                                        _i64, _vp, _vp, _vp]
         L.hh_status_string.argtypes = [_int]
@@ -289,6 +293,20 @@ def hh_update_microbench(ctx, variant: int, updates: int, threads: int, out=None
                                              _stream_ptr(stream, ctx.device))
     _check(st, "hh_update_microbench")
     return out
+
+
+def hh_autotune(ctx, max_device_bytes: int = 1 << 30) -> None:
+    _check(load_library().hh_autotune(ctx.ptr, int(max_device_bytes)), "hh_autotune")
+
+
+def hh_tune_save(ctx, path: str) -> None:
+    _check(load_library().hh_tune_save(ctx.ptr, path.encode()), "hh_tune_save")
+
+
+def hh_tune_describe(ctx) -> str:
+    buf = ctypes.create_string_buffer(8192)
+    _check(load_library().hh_tune_describe(ctx.ptr, buf, len(buf)), "hh_tune_describe")
+    return buf.value.decode()
 
 
 def hh_last_launch_count(ctx) -> int:

@@ -70,6 +70,9 @@ def test_null_context_is_rejected_without_cuda(lib):
     assert L.hh_init(None, 0, None) == hh.HH_ERR_INVALID_ARG
     assert L.hh_hash_segments(None, 64, None, 1, None, None, 0, None, None, 1, None, None,
                               None) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_autotune(None, 1 << 30) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_tune_save(None, b"x") == hh.HH_ERR_INVALID_ARG
+    assert L.hh_tune_describe(None, None, 0) == hh.HH_ERR_INVALID_ARG
 
 
 def test_init_without_a_gpu_reports_no_device(lib):
