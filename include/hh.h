@@ -235,13 +235,16 @@ int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages,
 /*
  * Integer-issue microbenchmark (no counterpart in the paper; it measures the
  * ceiling the integer pipes put on Section 4.2's Update).  Each of `threads`
- * threads (a multiple of 256) runs `updates` Updates on register state with
- * no memory traffic and writes one word to out[thread] (device uint64
- * [threads]).  `variant` 0..HH_UPDATE_VARIANTS-1 selects how the 64-bit adds
- * are split between the ALU and FMA pipes; every variant gives identical
- * output words.
+ * threads (a multiple of 32; of 256 when above 256) runs `updates` Updates
+ * on register state with no memory traffic and writes one word to
+ * out[thread] (device uint64 [threads]).  Variants 0..4 keep the whole
+ * four-lane state in one thread and split the 64-bit adds differently
+ * between the ALU and FMA pipes; variants 5..9 are the same five splits for
+ * one lane pair per thread (how messages of 128 KiB and more run).  The
+ * variants of each group give identical output words.  With few threads it
+ * measures the time of one Update chain rather than the pipes' throughput.
  */
-#define HH_UPDATE_VARIANTS 5
+#define HH_UPDATE_VARIANTS 10
 int hh_update_microbench(hh_ctx* ctx, int variant, int64_t updates, int64_t threads,
                          uint64_t* out, void* stream);
 
@@ -252,11 +255,28 @@ int hh_update_microbench(hh_ctx* ctx, int variant, int64_t updates, int64_t thre
  * and keeps, in ctx, the fastest per length regime: for fixed-length
  * batches per length class (<= 64, <= 256, <= 1024, <= 8192 bytes, larger)
  * the TMA kernel's window, pipeline depth and messages per thread; for
- * ragged batches the warp-tile kernel's window and depth; and the message
- * length above which a message runs two threads per message (or never).
+ * ragged batches the warp-tile kernel's window and depth; the message
+ * length from which a message runs two threads per message (or never); and
+ * up to how many such messages per SM each gets a warp of its own.
  * Synchronous; takes seconds.  Results are identical whatever is chosen.
  */
 int hh_autotune(hh_ctx* ctx, int64_t max_device_bytes);
+
+/*
+ * Set one scalar of ctx's tuning table (the shapes are set with
+ * hh_set_staged_shape).  Names and ranges:
+ *   "huge_bucket"  0..4096: length-sort bucket from which messages run two
+ *                  threads per message (4096: never; default 2176, 128 KiB);
+ *   "solo_per_sm"  0..64: while at most this many such messages per SM are
+ *                  in a launch, each gets a warp of its own (0: never;
+ *                  default 4);
+ *   "solo_shared"  0/1: whether those one-per-warp tiles are also used while
+ *                  other launches with such messages are in flight (default
+ *                  1).
+ * HH_ERR_INVALID_ARG for another name or a value out of range.  Results
+ * never depend on these settings.
+ */
+int hh_set_tune_param(hh_ctx* ctx, const char* name, int value);
 
 /* Write ctx's tuning table as text (hh_init reads it back). */
 int hh_tune_save(hh_ctx* ctx, const char* path);

@@ -8,7 +8,9 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "hh.h"
 #include "hh_context.h"
@@ -16,7 +18,9 @@
 
 namespace {
 
-constexpr int64_t kSortMinMessages = 1024;        // below this, index order is fine
+// Every ragged batch is length-sorted (one launch up to 8192 messages): the
+// sort also finds the long messages that run two threads each.
+constexpr int64_t kSortMinMessages = 1;
 constexpr int64_t kMaxSortedMessages = 0x7FFFFFFFll;
 constexpr size_t kHostChunkBytes = size_t(64) << 20;  // payload per host-path chunk
 constexpr int64_t kHostChunkMessages = int64_t(1) << 20;
@@ -117,9 +121,13 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
       ctx->last_launches += 1;
       q.skip_if_short = 1;
     }
-    // The grid is sized for warp tiles of 32; pair tiles (16 messages) are
+    // The grid is sized for warp tiles of 32, or for up to solo_max solo
+    // tiles (one message each) when that is more; solo and pair tiles are
     // taken from the same queue by the same persistent CTAs.
-    q.tiles = (n + 31) / 32;
+    q.solo_max = sort ? static_cast<int64_t>(ctx->tune.solo_per_sm) * ctx->num_sms : 0;
+    q.solo_ctas = static_cast<int>((q.solo_max + hh::kRaggedWarps - 1) / hh::kRaggedWarps);
+    q.solo_shared = ctx->tune.solo_shared;
+    q.tiles = std::max((n + 31) / 32, std::min(n, q.solo_max));
     e = hh::launch_ragged(b, q, ctx->tune.ragged, ctx->num_sms, stream);
   }
   ctx->last_launches += 1;
@@ -165,7 +173,42 @@ int grow(T** p, size_t* cap, size_t need) {
   return HH_OK;
 }
 
+struct OccupancyEntry {
+  const void* kern;
+  int device, threads, smem, per_sm;
+};
+std::mutex g_occupancy_mu;
+std::vector<OccupancyEntry> g_occupancy;
+
 }  // namespace
+
+namespace hh {
+
+int blocks_per_sm(const void* kern, int threads, int smem, cudaError_t* err) {
+  *err = cudaSuccess;
+  int dev = 0;
+  if ((*err = cudaGetDevice(&dev)) != cudaSuccess) return 0;
+  {
+    std::lock_guard<std::mutex> lock(g_occupancy_mu);
+    for (const OccupancyEntry& e : g_occupancy)
+      if (e.kern == kern && e.device == dev && e.threads == threads && e.smem == smem)
+        return e.per_sm;
+  }
+  if (smem > 0 &&
+      (*err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+          cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  if ((*err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) !=
+      cudaSuccess)
+    return 0;
+  if (per_sm < 1) per_sm = 1;
+  std::lock_guard<std::mutex> lock(g_occupancy_mu);
+  g_occupancy.push_back({kern, dev, threads, smem, per_sm});
+  return per_sm;
+}
+
+}  // namespace hh
 
 extern "C" {
 
@@ -204,13 +247,13 @@ int hh_init(hh_ctx** out, int device, const char* tune_cache_path) {
     return HH_ERR_INVALID_ARG;
   }
   bool ok = cudaMalloc(&ctx->d_err, sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&ctx->d_next_tile, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc(&ctx->d_next_tile, 4 * sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&ctx->d_use_perm, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&ctx->d_huge, sizeof(long long)) == cudaSuccess &&
             cudaMalloc(&ctx->d_hist, sizeof(uint32_t) * hh::kBuckets) == cudaSuccess &&
             cudaMalloc(&ctx->d_cursor, sizeof(uint32_t) * hh::kBuckets) == cudaSuccess &&
             cudaMemset(ctx->d_err, 0, sizeof(int)) == cudaSuccess &&
-            cudaMemset(ctx->d_next_tile, 0, sizeof(unsigned long long)) == cudaSuccess;
+            cudaMemset(ctx->d_next_tile, 0, 4 * sizeof(unsigned long long)) == cudaSuccess;
   if (!ok) {
     hh_destroy(ctx);
     return HH_ERR_NO_MEMORY;
@@ -437,8 +480,9 @@ int hh_last_launch_count(hh_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
 
 int hh_update_microbench(hh_ctx* ctx, int variant, int64_t updates, int64_t threads,
                          uint64_t* out, void* stream) {
-  if (ctx == nullptr || out == nullptr || updates < 0 || threads <= 0 || threads % 256 != 0 ||
-      threads / 256 > INT32_MAX || variant < 0 || variant >= HH_UPDATE_VARIANTS)
+  if (ctx == nullptr || out == nullptr || updates < 0 || threads <= 0 || threads % 32 != 0 ||
+      (threads > 256 && threads % 256 != 0) || threads / 256 > INT32_MAX || variant < 0 ||
+      variant >= HH_UPDATE_VARIANTS)
     return HH_ERR_INVALID_ARG;
   DeviceGuard guard(ctx->device);
   if (!guard.ok) return HH_ERR_CUDA;

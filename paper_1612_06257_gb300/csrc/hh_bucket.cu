@@ -14,7 +14,8 @@
 // non-empty bucket; a one-block exclusive scan in descending bucket order
 // (which also resets the tile counter of the work queue); and a scatter that
 // ranks elements inside each 8192-element chunk in shared memory and reserves
-// each bucket's range with one global atomic per chunk.  The order inside a
+// each bucket's range with one global atomic per chunk.  A batch of at most
+// one chunk is sorted by a single block in one launch.  The order inside a
 // bucket depends on atomic timing; results do not, because every message's
 // hash is stored at its own index.
 #include <cuda_runtime.h>
@@ -65,13 +66,16 @@ __global__ void __launch_bounds__(kSortThreads) bucket_count_kernel(Batch b, uin
     if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
-// cursor[k] = number of messages in buckets above k (descending order).
-__global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_t* hist,
-                                                                   uint32_t* cursor,
-                                                                   unsigned long long* next_tile,
-                                                                   int* use_perm,
-                                                                   long long* huge_count,
-                                                                   int huge_bucket) {
+// Exclusive scan of counts[] in descending bucket order: cursor[k] = number
+// of messages in buckets above k.  Also resets the work queue's counters
+// next_tile[0..3] (warp tiles, huge-prefix claims, launch bookkeeping); writes the number of messages in buckets >=
+// huge_bucket (the huge count; 0 when huge_bucket >= kBuckets) and the
+// use-order flag (1 when some message is longer than kShortMax), and returns
+// that flag.  Called by all kSortThreads threads of one block; counts and
+// cursor may be shared or global memory.
+__device__ __forceinline__ int scan_descending(const uint32_t* counts, uint32_t* cursor,
+                                               unsigned long long* next_tile, int* use_perm,
+                                               long long* huge_count, int huge_bucket) {
   constexpr int kPer = kBuckets / kSortThreads;  // 4 buckets per thread
   __shared__ uint32_t warp_sums[kSortThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -81,7 +85,7 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_
   uint32_t local = 0;
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
-    v[j] = hist[kBuckets - 1 - (tid * kPer + j)];
+    v[j] = counts[kBuckets - 1 - (tid * kPer + j)];
     local += v[j];
   }
   uint32_t incl = local;
@@ -113,8 +117,11 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_
     if (bucket == huge_bucket) *huge_count = static_cast<long long>(run);
   }
   if (tid == 0) {
-    *next_tile = 0ull;
-    if (huge_bucket >= kBuckets) *huge_count = 0;  // pair tiles switched off
+    next_tile[0] = 0ull;
+    next_tile[1] = 0ull;
+    next_tile[2] = 0ull;  // launch bookkeeping of the hash kernel
+    next_tile[3] = 0ull;
+    if (huge_bucket >= kBuckets) *huge_count = 0;  // huge messages switched off
   }
   // Buckets above kShortMax / 32 hold messages longer than kShortMax bytes.
   const int long_bucket = kShortMax / 32 + 1;
@@ -124,6 +131,58 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_
     mine |= v[j] != 0 && kBuckets - 1 - (tid * kPer + j) >= long_bucket;
   const int any_long = __syncthreads_or(mine);
   if (tid == 0) *use_perm = any_long;
+  return any_long;
+}
+
+__global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_t* hist,
+                                                                   uint32_t* cursor,
+                                                                   unsigned long long* next_tile,
+                                                                   int* use_perm,
+                                                                   long long* huge_count,
+                                                                   int huge_bucket) {
+  scan_descending(hist, cursor, next_tile, use_perm, huge_count, huge_bucket);
+}
+
+// Ranks of chunk elements c .. c + kChunk - 1 inside their buckets: counts
+// into cnt[] (shared, zeroed by the caller) and returns each element's key
+// (-1 past the end) and rank.
+__device__ __forceinline__ void rank_chunk(const Batch& b, int64_t n, int64_t c, uint32_t* cnt,
+                                           int key[kPerThread], uint32_t rank[kPerThread]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int e = 0; e < kPerThread; ++e) {
+    const int64_t i = c + e * kSortThreads + threadIdx.x;
+    key[e] = i < n ? bucket_of(b, i) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, key[e]);
+    const int leader = __ffs(peers) - 1;
+    uint32_t first = 0;
+    if (key[e] >= 0 && lane == leader) first = atomicAdd(&cnt[key[e]], __popc(peers));
+    first = __shfl_sync(0xffffffffu, first, leader);
+    rank[e] = first + __popc(peers & lanemask_lt());
+  }
+}
+
+// The whole sort of a batch of at most kChunk messages in one block: rank
+// in shared memory, scan, scatter.
+__global__ void __launch_bounds__(kSortThreads) bucket_small_kernel(
+    Batch b, int32_t* perm, unsigned long long* next_tile, int* use_perm,
+    long long* huge_count, int huge_bucket) {
+  resolve_count(b);
+  const int64_t n = b.n < kChunk ? b.n : kChunk;  // the host checked b.n <= kChunk
+  __shared__ uint32_t cnt[kBuckets];
+  __shared__ uint32_t base[kBuckets];
+  for (int i = threadIdx.x; i < kBuckets; i += kSortThreads) cnt[i] = 0;
+  __syncthreads();
+  int key[kPerThread];
+  uint32_t rank[kPerThread];
+  rank_chunk(b, n, 0, cnt, key, rank);
+  __syncthreads();
+  if (!scan_descending(cnt, base, next_tile, use_perm, huge_count, huge_bucket)) return;
+#pragma unroll
+  for (int e = 0; e < kPerThread; ++e) {
+    const int64_t i = e * kSortThreads + threadIdx.x;
+    if (key[e] >= 0) perm[base[key[e]] + rank[e]] = static_cast<int32_t>(i);
+  }
 }
 
 __global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(Batch b, uint32_t* cursor,
@@ -134,24 +193,13 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(Batch b, u
   const int64_t n = b.n;
   __shared__ uint32_t cnt[kBuckets];
   __shared__ uint32_t base[kBuckets];
-  const int lane = threadIdx.x & 31;
   for (int64_t c = static_cast<int64_t>(blockIdx.x) * kChunk; c < n;
        c += static_cast<int64_t>(gridDim.x) * kChunk) {
     for (int i = threadIdx.x; i < kBuckets; i += kSortThreads) cnt[i] = 0;
     __syncthreads();
     int key[kPerThread];
     uint32_t rank[kPerThread];
-#pragma unroll
-    for (int e = 0; e < kPerThread; ++e) {
-      const int64_t i = c + e * kSortThreads + threadIdx.x;
-      key[e] = i < n ? bucket_of(b, i) : -1;
-      const unsigned peers = __match_any_sync(0xffffffffu, key[e]);
-      const int leader = __ffs(peers) - 1;
-      uint32_t first = 0;
-      if (key[e] >= 0 && lane == leader) first = atomicAdd(&cnt[key[e]], __popc(peers));
-      first = __shfl_sync(0xffffffffu, first, leader);
-      rank[e] = first + __popc(peers & lanemask_lt());
-    }
+    rank_chunk(b, n, c, cnt, key, rank);
     __syncthreads();
     for (int i = threadIdx.x; i < kBuckets; i += kSortThreads)
       if (cnt[i]) base[i] = atomicAdd(&cursor[i], cnt[i]);
@@ -172,6 +220,12 @@ cudaError_t launch_bucket_sort(const Batch& b, uint32_t* hist,
                                int* use_perm, long long* huge_count, int huge_bucket,
                                int num_sms, cudaStream_t stream, int* launches) {
   const int64_t n = b.n;
+  if (n <= kChunk) {
+    bucket_small_kernel<<<1, kSortThreads, 0, stream>>>(b, perm, next_tile, use_perm, huge_count,
+                                                         huge_bucket);
+    *launches += 1;
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kBuckets, stream);
   if (e != cudaSuccess) return e;
   const int64_t chunks = (n + kChunk - 1) / kChunk;

@@ -42,6 +42,8 @@ struct TuneTable {
                                       {256, 2, 1}};
   StagedShape ragged{256, 2};  // warp-tile kernel
   int huge_bucket = kHugeBucket;  // messages in this bucket and above run two threads each
+  int solo_per_sm = kSoloPerSm;   // up to this many huge messages per SM: one warp each
+  int solo_shared = 1;            // 1: solo tiles also beside other launches in flight
 };
 
 // Read a table written by hh_tune_save; false (t unchanged) on a bad file.
@@ -54,7 +56,7 @@ struct hh_ctx {
   int num_sms = 0;
   int kernel = HH_KERNEL_AUTO;
   int* d_err = nullptr;
-  unsigned long long* d_next_tile = nullptr;
+  unsigned long long* d_next_tile = nullptr;  // [4]: the work queue's counters
   int* d_use_perm = nullptr;
   long long* d_huge = nullptr;
   uint32_t* d_hist = nullptr;

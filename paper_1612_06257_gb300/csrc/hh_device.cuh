@@ -113,56 +113,64 @@ __device__ __forceinline__ void zipper_pair(uint64_t a, uint64_t b, uint64_t& za
 //   2: as 1, and v1 += ZM(v0) on the FMA pipe.
 //   3: v0 += mul1 on the ALU, v0 += ZM(v1) and v1 += ZM(v0) on the FMA pipe.
 //   4: as 3, and v1 += packet + mul0 on the FMA pipe as well.
-template <int V>
-__device__ __forceinline__ void update_v(State& s, const uint64_t p[4], uint32_t one) {
+template <int V, int N>
+__device__ __forceinline__ void update_lanes(uint64_t (&v0)[N], uint64_t (&v1)[N],
+                                             uint64_t (&mul0)[N], uint64_t (&mul1)[N],
+                                             const uint64_t (&p)[N], uint32_t one) {
+  static_assert(N == 2 || N == 4, "lanes come in ZipperMerge pairs");
   if constexpr (V == 0) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      s.v1[i] += p[i] + s.mul0[i];
-      s.mul0[i] ^= mul_lo(s.v1[i], s.v0[i] >> 32);
-      s.v0[i] += s.mul1[i];
-      s.mul1[i] ^= mul_lo(s.v0[i], s.v1[i] >> 32);
+    for (int i = 0; i < N; ++i) {
+      v1[i] += p[i] + mul0[i];
+      mul0[i] ^= mul_lo(v1[i], v0[i] >> 32);
+      v0[i] += mul1[i];
+      mul1[i] ^= mul_lo(v0[i], v1[i] >> 32);
     }
-    zipper_add_pair(s.v0[0], s.v0[1], s.v1[0], s.v1[1]);
-    zipper_add_pair(s.v0[2], s.v0[3], s.v1[2], s.v1[3]);
-    zipper_add_pair(s.v1[0], s.v1[1], s.v0[0], s.v0[1]);
-    zipper_add_pair(s.v1[2], s.v1[3], s.v0[2], s.v0[3]);
+#pragma unroll
+    for (int i = 0; i < N; i += 2) zipper_add_pair(v0[i], v0[i + 1], v1[i], v1[i + 1]);
+#pragma unroll
+    for (int i = 0; i < N; i += 2) zipper_add_pair(v1[i], v1[i + 1], v0[i], v0[i + 1]);
   } else {
-  // V 1-2: add[i] = mul1 before its update (v0 + add + ZM(v1) is one 3-input
-  // add later).  V 3-4: add[i] = v0 + mul1, formed now.
-  uint64_t add[4];
+    // V 1-2: add[i] = mul1 before its update (v0 + add + ZM(v1) is one
+    // 3-input add later).  V 3-4: add[i] = v0 + mul1, formed now.
+    uint64_t add[N];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    if (V == 4) s.v1[i] = add_on_fma(add_on_fma(s.v1[i], p[i], one), s.mul0[i], one);
-    else s.v1[i] += p[i] + s.mul0[i];
-    s.mul0[i] ^= mul_lo(s.v1[i], s.v0[i] >> 32);
-    if (V >= 3) {
-      add[i] = s.v0[i] + s.mul1[i];
-      s.mul1[i] ^= mul_lo(add[i], s.v1[i] >> 32);
-    } else {
-      add[i] = s.mul1[i];
-      const uint32_t lo = lo32(s.v0[i]) + lo32(add[i]);  // lo(v0 + mul1)
-      s.mul1[i] ^= static_cast<uint64_t>(lo) * hi32(s.v1[i]);
+    for (int i = 0; i < N; ++i) {
+      if (V == 4) v1[i] = add_on_fma(add_on_fma(v1[i], p[i], one), mul0[i], one);
+      else v1[i] += p[i] + mul0[i];
+      mul0[i] ^= mul_lo(v1[i], v0[i] >> 32);
+      if (V >= 3) {
+        add[i] = v0[i] + mul1[i];
+        mul1[i] ^= mul_lo(add[i], v1[i] >> 32);
+      } else {
+        add[i] = mul1[i];
+        const uint32_t lo = lo32(v0[i]) + lo32(add[i]);  // lo(v0 + mul1)
+        mul1[i] ^= static_cast<uint64_t>(lo) * hi32(v1[i]);
+      }
     }
-  }
-  uint64_t z[4];
-  zipper_pair(s.v1[0], s.v1[1], z[0], z[1]);
-  zipper_pair(s.v1[2], s.v1[3], z[2], z[3]);
+    uint64_t z[N];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-    s.v0[i] = (V >= 3) ? add_on_fma(add[i], z[i], one) : s.v0[i] + add[i] + z[i];
-  zipper_pair(s.v0[0], s.v0[1], z[0], z[1]);
-  zipper_pair(s.v0[2], s.v0[3], z[2], z[3]);
+    for (int i = 0; i < N; i += 2) zipper_pair(v1[i], v1[i + 1], z[i], z[i + 1]);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) s.v1[i] = (V >= 2) ? add_on_fma(s.v1[i], z[i], one) : s.v1[i] + z[i];
+    for (int i = 0; i < N; ++i)
+      v0[i] = (V >= 3) ? add_on_fma(add[i], z[i], one) : v0[i] + add[i] + z[i];
+#pragma unroll
+    for (int i = 0; i < N; i += 2) zipper_pair(v0[i], v0[i + 1], z[i], z[i + 1]);
+#pragma unroll
+    for (int i = 0; i < N; ++i) v1[i] = (V >= 2) ? add_on_fma(v1[i], z[i], one) : v1[i] + z[i];
   }
+}
+
+template <int V>
+__device__ __forceinline__ void update_v(State& s, const uint64_t (&p)[4], uint32_t one) {
+  update_lanes<V, 4>(s.v0, s.v1, s.mul0, s.mul1, p, one);
 }
 
 // The variant every kernel uses: fastest in the Update-rate microbenchmark on
 // GB300 (all ALU; moving adds to IMAD.WIDE was slower).
 constexpr int kFastUpdate = 1;
 
-__device__ __forceinline__ void update(State& s, const uint64_t p[4]) {
+__device__ __forceinline__ void update(State& s, const uint64_t (&p)[4]) {
   update_v<kFastUpdate>(s, p, 1u);
 }
 
@@ -235,25 +243,15 @@ __device__ __forceinline__ void init_half(Half& s, const uint64_t key[4], int ha
   }
 }
 
-// Update of one lane pair (the same statement order as update_v<1>).
-__device__ __forceinline__ void update_half(Half& s, uint64_t p0, uint64_t p1) {
+// Update of one lane pair (variant V as for update_v).
+template <int V>
+__device__ __forceinline__ void update_half_v(Half& s, uint64_t p0, uint64_t p1, uint32_t one) {
   const uint64_t p[2] = {p0, p1};
-  uint64_t add[2];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    s.v1[i] += p[i] + s.mul0[i];
-    s.mul0[i] ^= mul_lo(s.v1[i], s.v0[i] >> 32);
-    add[i] = s.mul1[i];
-    const uint32_t lo = lo32(s.v0[i]) + lo32(add[i]);  // lo(v0 + mul1)
-    s.mul1[i] ^= static_cast<uint64_t>(lo) * hi32(s.v1[i]);
-  }
-  uint64_t z[2];
-  zipper_pair(s.v1[0], s.v1[1], z[0], z[1]);
-#pragma unroll
-  for (int i = 0; i < 2; ++i) s.v0[i] = s.v0[i] + add[i] + z[i];
-  zipper_pair(s.v0[0], s.v0[1], z[0], z[1]);
-#pragma unroll
-  for (int i = 0; i < 2; ++i) s.v1[i] += z[i];
+  update_lanes<V, 2>(s.v0, s.v1, s.mul0, s.mul1, p, one);
+}
+
+__device__ __forceinline__ void update_half(Half& s, uint64_t p0, uint64_t p1) {
+  update_half_v<kFastUpdate>(s, p0, p1, 1u);
 }
 
 __device__ __forceinline__ void inject_size_half(Half& s, uint32_t r) {

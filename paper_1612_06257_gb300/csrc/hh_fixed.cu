@@ -231,12 +231,9 @@ cudaError_t launch_fixed_t(const CUtensorMap& tmap, const FixedParams& p, int nu
                            cudaStream_t stream) {
   using L = FixedLayout<W, NST, M>;
   auto kern = fixed_tma_kernel<W, NST, M>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+  cudaError_t e;
+  const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), kRows, L::kBytes, &e);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRows, L::kBytes);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
   const int64_t tiles = (p.n + kRows * M - 1) / (kRows * M);
   const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
   const int grid = static_cast<int>(tiles < cap ? tiles : cap);

@@ -56,9 +56,20 @@ struct Queue {
   const int* use_perm;       // device flag: 0 = ignore perm (no long message), or null
   int skip_if_short = 0;     // 1: return at once when *use_perm == 0 (the short kernel runs)
   const long long* huge_count = nullptr;  // messages perm[0 .. *huge_count) run as pairs
-  unsigned long long* next_tile;  // atomic tile counter (sorted order), or null = static
-  int64_t tiles;
+  unsigned long long* next_tile;  // [4] (sorted order): [0] warp-tile counter, [1] huge-
+                                  // prefix claims, [2..3] launch bookkeeping; or null =
+                                  // static order
+  int64_t tiles;             // tiles the grid is sized for
+  int64_t solo_max = 0;      // huge prefixes of at most this many messages run one per warp
+  int solo_ctas = 0;         // ... taken only by the warps of blocks 0 .. solo_ctas - 1
+  int solo_shared = 0;       // 1: solo tiles also while other such launches are in flight
 };
+
+// Solo tiles (one huge message per warp) while there are at most this many
+// huge messages per SM: one per warp scheduler.  Beyond that, warps would
+// share schedulers and 16-message pair tiles give more throughput.
+constexpr int kSoloPerSm = 4;
+constexpr int kRaggedWarps = 4;  // warps per block of the ragged kernel
 
 // Staged-kernel shapes: bytes of each message staged per pipeline step (W)
 // and the number of pipeline buffers.
@@ -69,6 +80,12 @@ struct StagedShape {
 };
 
 // Launchers (return the CUDA error of the launch).
+// Resident blocks per SM of `kern` at this block size and dynamic shared
+// memory on the current device; sets the kernel's dynamic shared memory
+// limit first.  Cached per (kernel, device, threads, smem), so only the
+// first launch of a shape pays for the queries.  0 on error (in *err).
+int blocks_per_sm(const void* kern, int threads, int smem, cudaError_t* err);
+
 cudaError_t launch_naive(const Batch& b, cudaStream_t stream);
 cudaError_t launch_staged(const Batch& b, const Queue& q, StagedShape shape, bool aligned16,
                           int num_sms, cudaStream_t stream);

@@ -279,16 +279,9 @@ template <int W, int NST, bool kAligned>
 cudaError_t launch_staged_t(const Batch& b, const Queue& q, int num_sms, cudaStream_t stream) {
   using L = StagedLayout<W, NST>;
   auto kern = staged_kernel<W, NST, kAligned>;
-  static bool configured = false;  // attribute set once per process and instantiation
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileRows, L::kBytes);
+  cudaError_t e;
+  const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), kTileRows, L::kBytes, &e);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
   const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
   const int grid = static_cast<int>(q.tiles < cap ? q.tiles : cap);
   if (grid <= 0) return cudaSuccess;
@@ -299,15 +292,10 @@ cudaError_t launch_staged_t(const Batch& b, const Queue& q, int num_sms, cudaStr
 template <int W, int NST>
 int blocks_per_sm_t(bool aligned) {
   using L = StagedLayout<W, NST>;
-  int per_sm = 0;
-  if (aligned) {
-    cudaFuncSetAttribute(staged_kernel<W, NST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, staged_kernel<W, NST, true>, kTileRows, L::kBytes);
-  } else {
-    cudaFuncSetAttribute(staged_kernel<W, NST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, staged_kernel<W, NST, false>, kTileRows, L::kBytes);
-  }
-  return per_sm;
+  cudaError_t e;
+  const void* kern = aligned ? reinterpret_cast<const void*>(staged_kernel<W, NST, true>)
+                             : reinterpret_cast<const void*>(staged_kernel<W, NST, false>);
+  return blocks_per_sm(kern, kTileRows, L::kBytes, &e);
 }
 
 }  // namespace

@@ -28,7 +28,7 @@ struct Scratch {
   int32_t perm[kMaxMessages];
   uint32_t hist[hh::kBuckets];
   uint32_t cursor[hh::kBuckets];
-  unsigned long long next_tile;
+  unsigned long long next_tile[4];
   long long huge_count;
   int use_perm;
   int err;
@@ -101,15 +101,17 @@ extern "C" int hh_hash_batch_noalloc(int bits, const uint64_t* keys, int key_mod
   // counter and the flag, so nothing left by an earlier call is read.
   int launches = 0;
   cudaError_t e = hh::launch_bucket_sort(b, scr->hist, scr->cursor, scr->perm,
-                                         &scr->next_tile, &scr->use_perm, &scr->huge_count,
+                                         scr->next_tile, &scr->use_perm, &scr->huge_count,
                                          hh::kHugeBucket, slot->num_sms, s, &launches);
   if (e != cudaSuccess) return HH_ERR_CUDA;
   hh::Queue q{};
   q.perm = scr->perm;
   q.use_perm = &scr->use_perm;
   q.huge_count = &scr->huge_count;
-  q.next_tile = &scr->next_tile;
-  q.tiles = (n + 31) / 32;
+  q.next_tile = scr->next_tile;
+  q.solo_max = static_cast<int64_t>(hh::kSoloPerSm) * slot->num_sms;
+  q.solo_ctas = static_cast<int>((q.solo_max + hh::kRaggedWarps - 1) / hh::kRaggedWarps);
+  q.tiles = (n + 31) / 32 > q.solo_max ? (n + 31) / 32 : (n < q.solo_max ? n : q.solo_max);
   e = hh::launch_ragged(b, q, hh::StagedShape{256, 2}, slot->num_sms, s);
   return e == cudaSuccess ? HH_OK : HH_ERR_CUDA;
 }

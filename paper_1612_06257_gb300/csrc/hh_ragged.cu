@@ -179,12 +179,13 @@ __device__ __forceinline__ void read_half_packet(const uint8_t* row, uint32_t of
   }
 }
 
-// One pair tile: 16 messages of the huge prefix of the length order, two
-// lanes per message (lane 2s + h keeps lanes 2h, 2h+1 of message s's state).
+// One pair tile: messages [first, last) (at most 16) of the huge prefix of
+// the length order, two lanes per message (lane 2s + h keeps lanes 2h, 2h+1
+// of message first + s's state).
 // Each message's row spans two ring rows and holds a 2W-byte window.
 template <int W, int NST>
-__device__ __forceinline__ void pair_tile(const Batch& b, const int32_t* perm, int64_t tile,
-                                          int64_t huge, uint8_t* ring, uint32_t ring_s,
+__device__ __forceinline__ void pair_tile(const Batch& b, const int32_t* perm, int64_t first,
+                                          int64_t last, uint8_t* ring, uint32_t ring_s,
                                           uintptr_t base, uintptr_t safe_lo, uintptr_t safe_hi,
                                           int lane) {
   using L = RaggedLayout<W, NST>;
@@ -193,8 +194,8 @@ __device__ __forceinline__ void pair_tile(const Batch& b, const int32_t* perm, i
   constexpr int kChunks = WP / 16 + 1;
   constexpr int kPerLane = (kChunks + 3) / 4;
   const int slot = lane >> 1, half = lane & 1;
-  const int64_t idx = tile * 16 + slot;
-  const bool valid = idx < huge;
+  const int64_t idx = first + slot;
+  const bool valid = idx < last;
   int64_t m = 0, start = 0, len = 0;
   int bad = 0;
   uint64_t key[4] = {0, 0, 0, 0};
@@ -322,8 +323,153 @@ __device__ __forceinline__ void pair_tile(const Batch& b, const int32_t* perm, i
   __syncwarp();
 }
 
+// One solo tile: a single message of the huge prefix owns the whole warp.
+// Lanes 0 and 1 hash it (one lane pair each, as in a pair tile); all 32
+// lanes copy it.  The warp's ring is re-cut into kSoloStages stages of 8W
+// bytes, so about 14 KiB (W = 256) of the message is in flight and the
+// copies never hold up the Update chain, which then runs at the rate one
+// warp issues it.  Used while the huge messages are few enough to get a
+// warp scheduler each (Queue::solo_max).
+constexpr int kSoloStages = 8;
+
+// Solo tiles running on this device, over every ragged kernel in flight,
+// the ragged launches with huge messages in flight, and which warp
+// schedulers run a solo tile (slot = 4 * SM + hardware warp slot mod 4).
+__device__ unsigned int g_solo_active = 0;
+__device__ unsigned int g_huge_kernels = 0;
+constexpr int kSchedulerSlots = 4096;
+__device__ unsigned int g_scheduler_solo[kSchedulerSlots];
+
+// This warp's scheduler slot (a placement hint only: results never depend
+// on it).
+__device__ __forceinline__ unsigned scheduler_slot() {
+  unsigned sm, warp;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+  asm volatile("mov.u32 %0, %%warpid;" : "=r"(warp));
+  return (4u * sm + (warp & 3u)) & (kSchedulerSlots - 1);
+}
+
+template <int W, int NST>
+__device__ __noinline__ void solo_tile(const Batch& b, const int32_t* perm, int64_t tile,
+                                          uint8_t* ring, uint32_t ring_s, uintptr_t base,
+                                          uintptr_t safe_lo, uintptr_t safe_hi, int lane) {
+  constexpr int SW = 8 * W;               // window bytes per stage
+  constexpr int kRow = SW + 16;           // 16-byte aligned span of a window
+  constexpr int kChunks = kRow / 16;
+  constexpr int kPerLane = (kChunks + 31) / 32;
+  static_assert(kSoloStages * kRow + 64 <= RaggedLayout<W, NST>::kWarpBytes,
+                "solo stages (and the read-past pad) must fit the warp's ring");
+  const int half = lane & 1;
+  const int64_t m = static_cast<int64_t>(perm[tile]);
+  int64_t start = 0, len = 0;
+  int bad = 0;
+  message_bounds(b, m, start, len, bad);
+  if (bad && lane == 0) record_error(b.err, bad);
+  uint64_t key[4];
+  const uint64_t* kp = key_of(b, m);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
+  Half s;
+  init_half(s, key, half);
+  const int64_t steps = (len + SW - 1) / SW;
+  const uintptr_t msg = base + start;
+  const uint32_t mis = static_cast<uint32_t>(msg & 15);
+  const int64_t packets = len >> 5;
+  const uint32_t r = static_cast<uint32_t>(len & 31);
+  const int64_t rem_step = r ? (packets * 32) / SW : -1;
+
+  auto issue = [&](int64_t k, int buf) {
+    const uintptr_t gs = msg + static_cast<uintptr_t>(k) * SW;
+    const int64_t wend = k * SW + SW < len ? k * SW + SW : len;
+    const uintptr_t ge = msg + static_cast<uintptr_t>(wend);
+    const uintptr_t a0 = gs & ~uintptr_t(15);
+    const uintptr_t a1 = (ge + 15) & ~uintptr_t(15);
+    const uintptr_t c0 = a0 > safe_lo ? a0 : safe_lo;
+    const uintptr_t c1 = a1 < safe_hi ? a1 : safe_hi;
+    uint32_t first = 0, end = 0;
+    if (c1 > c0) {
+      first = static_cast<uint32_t>((c0 - a0) >> 4);
+      end = static_cast<uint32_t>((c1 - a0) >> 4);
+    }
+    const uint32_t dst = ring_s + buf * kRow;
+#pragma unroll
+    for (int i = 0; i < kPerLane; ++i) {
+      const uint32_t c = static_cast<uint32_t>(lane + 32 * i);
+      if (c >= first && c < end)
+        cp_async16(dst + 16 * c, reinterpret_cast<const char*>(a0) + 16 * c);
+    }
+    // The (at most two) partial 16-byte blocks at the ends of the batch.
+    if (lane == 0 && (c0 > gs || c1 < ge || c1 <= c0)) {
+      uint8_t* row = ring + buf * kRow;
+      for (uintptr_t p = gs; p < ge; ++p)
+        if (p < c0 || p >= c1 || c1 <= c0) row[p - a0] = *reinterpret_cast<const uint8_t*>(p);
+    }
+    cp_async_commit();
+  };
+
+  int buf_issue = 0, buf_read = 0;
+  for (int64_t k = 0; k < kSoloStages - 1; ++k) {
+    if (k < steps) issue(k, buf_issue);
+    else cp_async_commit();
+    buf_issue = (buf_issue + 1 == kSoloStages) ? 0 : buf_issue + 1;
+  }
+  for (int64_t k = 0; k < steps; ++k) {
+    if (k + kSoloStages - 1 < steps) issue(k + kSoloStages - 1, buf_issue);
+    else cp_async_commit();
+    buf_issue = (buf_issue + 1 == kSoloStages) ? 0 : buf_issue + 1;
+    cp_async_wait<kSoloStages - 1>();
+    __syncwarp();
+    if (lane < 2) {
+      const uint8_t* row = ring + buf_read * kRow;
+      const int64_t left = packets - k * (SW / 32);
+      const int count = left < SW / 32 ? static_cast<int>(left) : SW / 32;
+      if (mis == 0) {
+#pragma unroll 4
+        for (int j = 0; j < count; ++j) {
+          uint64_t x0, x1;
+          read_half_packet<true>(row, 32u * j + 16u * half, x0, x1);
+          update_half(s, x0, x1);
+        }
+      } else {
+#pragma unroll 4
+        for (int j = 0; j < count; ++j) {
+          uint64_t x0, x1;
+          read_half_packet<false>(row, mis + 32u * j + 16u * half, x0, x1);
+          update_half(s, x0, x1);
+        }
+      }
+      if (k == rem_step) {
+        uint32_t w[8], rp[8];
+        read_packet<false>(row, mis + static_cast<uint32_t>(packets * 32 - k * SW), w);
+        remainder_packet(r, w, rp);
+        inject_size_half(s, r);
+        if (half == 0) update_half(s, join(rp[0], rp[1]), join(rp[2], rp[3]));
+        else update_half(s, join(rp[4], rp[5]), join(rp[6], rp[7]));
+      }
+    }
+    __syncwarp();
+    buf_read = (buf_read + 1 == kSoloStages) ? 0 : buf_read + 1;
+  }
+  cp_async_wait<0>();
+  finalize_half(s);
+  if (lane < 2) {
+    uint64_t h0 = s.v0[0] + s.v1[0] + s.mul0[0] + s.mul1[0];
+    uint64_t h1 = s.v0[1] + s.v1[1] + s.mul0[1] + s.mul1[1];
+    if (bad) h0 = h1 = 0;
+    uint64_t* o = b.out + m * b.words;
+    if (half == 0) {
+      o[0] = h0;
+      if (b.words >= 2) o[1] = h1;
+    } else if (b.words == 4) {
+      o[2] = h0;
+      o[3] = h1;
+    }
+  }
+  __syncwarp();
+}
+
 template <int W, int NST, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
+__global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q) {
   using L = RaggedLayout<W, NST>;
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -343,13 +489,77 @@ __global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
 
   if (q.skip_if_short && q.use_perm != nullptr && *q.use_perm == 0) return;  // short kernel runs
   const int32_t* perm = (q.perm && (q.use_perm == nullptr || *q.use_perm)) ? q.perm : nullptr;
-  // Tiles: first the pair tiles of the huge prefix of the length order (16
-  // messages each), then warp tiles of 32 messages.
+  // The huge prefix of the length order (messages perm[0 .. huge)) comes
+  // first, then warp tiles of 32 messages from counter next_tile[0].
   const int64_t huge = (perm != nullptr && q.huge_count != nullptr) ? *q.huge_count : 0;
-  const int64_t huge_tiles = (huge + 15) / 16;
-  const int64_t tiles = huge_tiles + (b.n - huge + 31) / 32;
+  const int64_t tiles = (b.n - huge + 31) / 32;
   int64_t static_tile = static_cast<int64_t>(blockIdx.x) * WARPS + warp;
   const int64_t static_step = static_cast<int64_t>(gridDim.x) * WARPS;
+
+  // Huge messages, longest first, claimed with fetch-and-add on
+  // next_tile[1]: a solo tile takes one message, a pair tile 16.  Solo
+  // tiles are taken only by warps of blocks 0 .. solo_ctas - 1 (the first
+  // wave places those blocks one per SM), on a warp scheduler that runs no
+  // other solo tile (g_scheduler_solo, over all launches in flight), while
+  // fewer than q.solo_max solo tiles run on the device (g_solo_active), and, unless q.solo_shared, only while no other launch
+  // with huge messages is in flight (g_huge_kernels, which a launch joins
+  // through next_tile[2] and leaves when its last warp, counted in
+  // next_tile[3], is done): under load, one message per warp would waste
+  // the issue slots that a pair tile shares among 16 messages.  Warps of
+  // other blocks skip this phase when solo tiles can take the whole prefix.
+  // Warps of the solo blocks leave it only when nothing is left, so every
+  // huge message is claimed.
+  if (huge > 0 && q.next_tile != nullptr) {
+    const bool eligible = q.solo_max > 0 && static_cast<int>(blockIdx.x) < q.solo_ctas;
+    int alone = 0;
+    if (lane == 0) {
+      if (atomicCAS(q.next_tile + 2, 0ull, 1ull) == 0ull) atomicAdd(&g_huge_kernels, 1u);
+      // 0 can be read while this launch's own join is still in flight.
+      alone = q.solo_shared || atomicAdd(&g_huge_kernels, 0u) <= 1u;
+    }
+    alone = __shfl_sync(kFull, alone, 0);
+    const bool all_solo = alone && huge <= q.solo_max;
+    const unsigned slot = scheduler_slot();
+    while (eligible || !all_solo) {
+      int kind = 0;  // 0: nothing left, 1: solo, 2: pair
+      long long first = 0, last = 0;
+      if (lane == 0) {
+        bool solo = false;
+        if (eligible && (q.solo_shared || atomicAdd(&g_huge_kernels, 0u) <= 1u)) {
+          // A solo tile needs a scheduler with no other solo tile on it.
+          solo = atomicCAS(&g_scheduler_solo[slot], 0u, 1u) == 0u;
+          if (solo && atomicAdd(&g_solo_active, 1u) >= static_cast<unsigned>(q.solo_max)) {
+            atomicSub(&g_solo_active, 1u);
+            atomicExch(&g_scheduler_solo[slot], 0u);
+            solo = false;
+          }
+        }
+        const unsigned long long take = solo ? 1ull : 16ull;
+        const long long f = static_cast<long long>(atomicAdd(q.next_tile + 1, take));
+        if (f < huge) {
+          kind = solo ? 1 : 2;
+          first = f;
+          last = f + static_cast<long long>(take) < huge ? f + static_cast<long long>(take) : huge;
+        } else if (solo) {
+          atomicSub(&g_solo_active, 1u);
+          atomicExch(&g_scheduler_solo[slot], 0u);
+        }
+      }
+      kind = __shfl_sync(kFull, kind, 0);
+      if (kind == 0) break;
+      first = __shfl_sync(kFull, first, 0);
+      last = __shfl_sync(kFull, last, 0);
+      if (kind == 1) {
+        solo_tile<W, NST>(b, perm, first, ring, ring_s, base, safe_lo, safe_hi, lane);
+        if (lane == 0) {
+          atomicSub(&g_solo_active, 1u);
+          atomicExch(&g_scheduler_solo[slot], 0u);
+        }
+      } else {
+        pair_tile<W, NST>(b, perm, first, last, ring, ring_s, base, safe_lo, safe_hi, lane);
+      }
+    }
+  }
 
   for (;;) {
     int64_t tile;
@@ -362,12 +572,8 @@ __global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
       static_tile += static_step;
     }
     if (tile >= tiles) break;
-    if (tile < huge_tiles) {
-      pair_tile<W, NST>(b, perm, tile, huge, ring, ring_s, base, safe_lo, safe_hi, lane);
-      continue;
-    }
 
-    const int64_t idx = huge + (tile - huge_tiles) * 32 + lane;
+    const int64_t idx = huge + tile * 32 + lane;
     const bool valid = idx < b.n;
     int64_t m = 0, start = 0, len = 0;
     int bad = 0;
@@ -492,6 +698,10 @@ __global__ void __launch_bounds__(WARPS * 32) ragged_kernel(Batch b, Queue q) {
     }
     __syncwarp();
   }
+  // The last warp of a launch with huge messages leaves g_huge_kernels.
+  if (huge > 0 && q.next_tile != nullptr && lane == 0 &&
+      atomicAdd(q.next_tile + 3, 1ull) == static_cast<unsigned long long>(gridDim.x) * WARPS - 1)
+    atomicSub(&g_huge_kernels, 1u);
 }
 
 // Thread per message for batches whose messages are all at most kShortMax
@@ -544,12 +754,9 @@ cudaError_t launch_ragged_t(const Batch& b, const Queue& q, int num_sms, cudaStr
   using L = RaggedLayout<W, NST>;
   constexpr int kBytes = WARPS * L::kWarpBytes;
   auto kern = ragged_kernel<W, NST, WARPS>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes);
+  cudaError_t e;
+  const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), WARPS * 32, kBytes, &e);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, kBytes);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
   const int64_t blocks_needed = (q.tiles + WARPS - 1) / WARPS;
   const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
   const int grid = static_cast<int>(blocks_needed < cap ? blocks_needed : cap);
@@ -561,10 +768,9 @@ cudaError_t launch_ragged_t(const Batch& b, const Queue& q, int num_sms, cudaStr
 }  // namespace
 
 cudaError_t launch_short(const Batch& b, const int* run_if, int num_sms, cudaStream_t stream) {
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, short_kernel, 256, 0);
+  cudaError_t e;
+  const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(short_kernel), 256, 0, &e);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
   const int64_t blocks = (b.n + 255) / 256;
   const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
   const int grid = static_cast<int>(blocks < cap ? blocks : cap);
@@ -584,7 +790,7 @@ bool ragged_shape_valid(StagedShape shape) {
 cudaError_t launch_ragged(const Batch& b, const Queue& q, StagedShape shape, int num_sms,
                           cudaStream_t stream) {
 #define HH_RAGGED(W_, N_) \
-  if (shape.window == W_ && shape.stages == N_) return launch_ragged_t<W_, N_, 4>(b, q, num_sms, stream);
+  if (shape.window == W_ && shape.stages == N_) return launch_ragged_t<W_, N_, kRaggedWarps>(b, q, num_sms, stream);
   HH_RAGGED_SHAPES(HH_RAGGED)
 #undef HH_RAGGED
   return cudaErrorInvalidValue;

@@ -7,8 +7,10 @@
 //     kernel's window, pipeline depth and messages per thread;
 //   * ragged batches (log-uniform lengths in [0, 65536]): the warp-tile
 //     kernel's window and pipeline depth;
-//   * very long messages (4 MiB buffers among short ones): the length above
-//     which a message runs two threads per message, or never.
+//   * long messages (log-uniform 64 KiB - 4 MiB after short ones): the length
+//     from which a message runs two threads per message, or never;
+//   * 8 long messages per SM: up to how many long messages per SM each gets
+//     a warp of its own (solo tiles) instead of sharing one (pair tiles).
 // The table can be written with hh_tune_save and read back by hh_init.
 #include <cuda_runtime.h>
 
@@ -133,6 +135,10 @@ const hh::StagedShape kRaggedCandidates[] = {HH_RAGGED_SHAPES(HH_LIST)};
 #undef HH_LIST
 
 }  // namespace
+
+namespace hh {
+bool set_tune_scalar(TuneTable& t, const char* name, int value);
+}
 
 extern "C" {
 
@@ -261,6 +267,43 @@ int hh_autotune(hh_ctx* ctx, int64_t max_device_bytes) {
     if (pick < 0) status = HH_ERR_CUDA;
   }
 
+  // Solo tiles: 8 huge messages per SM (log-uniform [128 KiB, 2 MiB]) after
+  // 4096 short ones; the candidates put the solo/pair boundary at 0 (pairs
+  // only), 1, 2, 4 or 8 huge messages per SM.
+  if (status == HH_OK) {
+    uint64_t state = 11;
+    off.assign(1, 0);
+    for (int i = 0; i < 4096; ++i) off.push_back(off.back() + 40);
+    const double lo = std::log(131072.0), hi = std::log(2097152.0);
+    for (int i = 0; i < 8 * ctx->num_sms; ++i) {
+      const double u = (next_random(state) >> 11) * (1.0 / 9007199254740992.0);
+      const int64_t len = static_cast<int64_t>(std::exp(lo + u * (hi - lo)));
+      if (off.back() + len > budget) break;
+      off.push_back(off.back() + len);
+    }
+    const int64_t n = static_cast<int64_t>(off.size()) - 1;
+    if (cudaMemcpy(buf.offsets, off.data(), sizeof(int64_t) * off.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      status = HH_ERR_CUDA;
+    const int candidates[5] = {0, 1, 2, 4, 8};
+    const int keep = ctx->tune.solo_per_sm;
+    const int pick =
+        status != HH_OK
+            ? -1
+            : fastest(
+                  5, [&](int i) { ctx->tune.solo_per_sm = candidates[i]; },
+                  [&] {
+                    return hh_hash64_batch(ctx, buf.keys, HH_KEY_SHARED, buf.bytes, buf.offsets,
+                                           n, buf.out, s);
+                  },
+                  s, ms);
+    std::snprintf(what, sizeof(what), "solo_per_sm (%lld messages, %lld B):",
+                  static_cast<long long>(n), static_cast<long long>(off.back()));
+    report_line(report, what, ms, [&](int i) { return std::to_string(candidates[i]); });
+    ctx->tune.solo_per_sm = pick < 0 ? keep : candidates[pick];
+    if (pick < 0) status = HH_ERR_CUDA;
+  }
+
   if (status == HH_OK && cudaStreamSynchronize(s) != cudaSuccess) status = HH_ERR_CUDA;
   if (s) cudaStreamDestroy(s);
   ctx->tune_report = status == HH_OK ? report : std::string();
@@ -283,10 +326,19 @@ int hh_tune_describe(hh_ctx* ctx, char* buf, int64_t buf_len) {
   text += line;
   std::snprintf(line, sizeof(line), "huge_bucket %d\n", ctx->tune.huge_bucket);
   text += line;
+  std::snprintf(line, sizeof(line), "solo_per_sm %d\n", ctx->tune.solo_per_sm);
+  text += line;
+  std::snprintf(line, sizeof(line), "solo_shared %d\n", ctx->tune.solo_shared);
+  text += line;
   text += ctx->tune_report;
   if (static_cast<int64_t>(text.size()) + 1 > buf_len) return HH_ERR_TOO_LARGE;
   std::memcpy(buf, text.c_str(), text.size() + 1);
   return HH_OK;
+}
+
+int hh_set_tune_param(hh_ctx* ctx, const char* name, int value) {
+  if (ctx == nullptr || name == nullptr) return HH_ERR_INVALID_ARG;
+  return hh::set_tune_scalar(ctx->tune, name, value) ? HH_OK : HH_ERR_INVALID_ARG;
 }
 
 int hh_tune_save(hh_ctx* ctx, const char* path) {
@@ -303,6 +355,24 @@ int hh_tune_save(hh_ctx* ctx, const char* path) {
 }  // extern "C"
 
 namespace hh {
+
+// Set one scalar entry of a tuning table; false for an unknown name or a
+// value out of range.
+bool set_tune_scalar(TuneTable& t, const char* name, int value) {
+  if (std::strcmp(name, "huge_bucket") == 0) {
+    if (value < 0 || value > kBuckets) return false;
+    t.huge_bucket = value;
+  } else if (std::strcmp(name, "solo_per_sm") == 0) {
+    if (value < 0 || value > 64) return false;
+    t.solo_per_sm = value;
+  } else if (std::strcmp(name, "solo_shared") == 0) {
+    if (value != 0 && value != 1) return false;
+    t.solo_shared = value;
+  } else {
+    return false;
+  }
+  return true;
+}
 
 // Parse a table written by hh_tune_save into `t`; false on any bad line.
 bool load_tune_table(const char* path, TuneTable& t) {
@@ -322,11 +392,9 @@ bool load_tune_table(const char* path, TuneTable& t) {
       const StagedShape sh{w, n, 1};
       ok = ragged_shape_valid(sh);
       if (ok) parsed.ragged = sh;
-    } else if (std::sscanf(line, "huge_bucket %d", &c) == 1) {
-      ok = c >= 0 && c <= kBuckets;
-      if (ok) parsed.huge_bucket = c;
     } else {
-      ok = false;
+      char name[32];
+      ok = std::sscanf(line, "%31s %d", name, &c) == 2 && set_tune_scalar(parsed, name, c);
     }
   }
   std::fclose(f);

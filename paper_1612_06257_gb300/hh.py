@@ -50,7 +50,7 @@ EXPORTS = (
     "hh_hash256_batch", "hh_hash_fixed", "hh_hash_host", "hh_get_device_error",
     "hh_set_kernel", "hh_last_launch_count", "hh_status_string", "hh_set_staged_shape",
     "hh_update_microbench", "hh_hash_batch_noalloc", "hh_hash_segments", "hh_autotune",
-    "hh_tune_save", "hh_tune_describe",
+    "hh_tune_save", "hh_tune_describe", "hh_set_tune_param",
 )
 
 HH_REGIME_FIXED = 0
@@ -101,6 +101,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.hh_hash_batch_noalloc.argtypes = [_int, _vp, _int, _vp, _vp, _i64, _vp, _vp, _vp]
         L.hh_autotune.argtypes = [_vp, _i64]
         L.hh_tune_save.argtypes = [_vp, ctypes.c_char_p]
+        L.hh_set_tune_param.argtypes = [_vp, ctypes.c_char_p, _int]
         L.hh_tune_describe.argtypes = [_vp, ctypes.c_char_p, _i64]
         L.hh_hash_segments.argtypes = [_vp, _int, _vp, ctypes.c_int32, _vp, _vp, _i64, _vp, _vp,
                                        _i64, _vp, _vp, _vp]
@@ -159,10 +160,13 @@ def _stream_ptr(stream, device):
     return stream.cuda_stream
 
 
+_I64 = (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ())
+
+
 def _dev_ptr(t, name, dtypes, device):
     if t is None:
         return None
-    if not t.is_cuda or t.device.index != device:
+    if t.get_device() != device:  # -1 for CPU tensors
         raise ValueError("%s must be a CUDA tensor on device %d" % (name, device))
     if t.dtype not in dtypes:
         raise ValueError("%s has dtype %s, expected one of %s" % (name, t.dtype, dtypes))
@@ -178,7 +182,7 @@ def _batch(fn_name, words, ctx, keys, key_mode, data, offsets, n=None, out=None,
     if out.numel() < n * words:
         raise ValueError("out holds %d words, need %d" % (out.numel(), n * words))
     dev = ctx.device
-    i64 = (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ())
+    i64 = _I64
     args = (ctx.ptr, _dev_ptr(keys, "keys", i64, dev), int(key_mode),
             _dev_ptr(data, "bytes", (torch.uint8,), dev),
             _dev_ptr(offsets, "offsets", (torch.int64,), dev), n,
@@ -207,7 +211,7 @@ def hh_hash_fixed(ctx, bits, keys, key_mode, data, msg_len, n, out=None, stream=
     if out is None:
         out = torch.empty(int(n) * words, dtype=torch.int64, device=data.device)
     dev = ctx.device
-    i64 = (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ())
+    i64 = _I64
     st = load_library().hh_hash_fixed(
         ctx.ptr, int(bits), _dev_ptr(keys, "keys", i64, dev), int(key_mode),
         _dev_ptr(data, "bytes", (torch.uint8,), dev), int(msg_len), int(n),
@@ -233,7 +237,7 @@ def hh_hash_segments(ctx, bits, key_table, key_index, data, starts, lengths, out
     if out is None:
         out = torch.empty(n * words, dtype=torch.int64, device=data.device)
     dev = ctx.device
-    i64 = (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ())
+    i64 = _I64
     st = load_library().hh_hash_segments(
         ctx.ptr, int(bits), _dev_ptr(key_table, "key_table", i64, dev),
         int(key_table.numel() // 4), _dev_ptr(key_index, "key_index", (torch.int32,), dev),
@@ -297,6 +301,11 @@ def hh_update_microbench(ctx, variant: int, updates: int, threads: int, out=None
 
 def hh_autotune(ctx, max_device_bytes: int = 1 << 30) -> None:
     _check(load_library().hh_autotune(ctx.ptr, int(max_device_bytes)), "hh_autotune")
+
+
+def hh_set_tune_param(ctx, name: str, value: int) -> None:
+    _check(load_library().hh_set_tune_param(ctx.ptr, name.encode(), int(value)),
+           "hh_set_tune_param")
 
 
 def hh_tune_save(ctx, path: str) -> None:

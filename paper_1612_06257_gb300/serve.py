@@ -16,6 +16,12 @@ measured per request from arrival to the moment its hashes are on the host.
 
 The keys and the batch descriptors live on the device; every hash step runs
 in libhh's kernels.
+
+Long messages (128 KiB and more) get a warp each while few of them run; with
+many batches in flight that is limited to 2 per SM (SERVING_SOLO_PER_SM),
+which gave the lowest p50 and p99 on the serving mix on GB300 (107 ms / 110-
+155 ms against 142 ms / 148-162 ms with two threads per message throughout)
+at the same saturation throughput.  A tuning table (`tune_path`) overrides it.
 """
 from __future__ import annotations
 
@@ -27,6 +33,8 @@ import numpy as np
 import torch
 
 from paper_1612_06257_gb300 import hh
+
+SERVING_SOLO_PER_SM = 2
 
 
 @dataclasses.dataclass
@@ -75,13 +83,15 @@ def plan_batch(queue, capacity: int, max_requests: int, bytes_free: int) -> int:
 class _Slot:
     """One stream, one hh context, fixed descriptor buffers, maybe a graph."""
 
-    def __init__(self, pool, bits, capacity, max_requests, device, use_graphs):
+    def __init__(self, pool, bits, capacity, max_requests, device, use_graphs, tune_path=None):
         self.words = bits // 64
         self.bits = bits
         self.capacity = capacity
         self.max_requests = max_requests
         dev = torch.device("cuda", device)
-        self.ctx = hh.hh_init(device)
+        self.ctx = hh.hh_init(device, tune_path)
+        if tune_path is None:
+            hh.hh_set_tune_param(self.ctx, "solo_per_sm", SERVING_SOLO_PER_SM)
         hh.hh_reserve(self.ctx, capacity)
         self.stream = torch.cuda.Stream(device=dev)
         self.pool = pool
@@ -177,7 +187,8 @@ class HashServer:
 
     def __init__(self, pool: torch.Tensor, *, bits: int = 64, slots: int = 4,
                  capacity: int = 1 << 16, max_requests_per_batch: int = 256,
-                 max_bytes_in_flight: int = 8 << 30, use_graphs: bool = True):
+                 max_bytes_in_flight: int = 8 << 30, use_graphs: bool = True,
+                 tune_path: str | None = None):
         if pool.dtype != torch.uint8 or not pool.is_cuda:
             raise ValueError("pool must be a CUDA uint8 tensor")
         self.pool = pool
@@ -186,8 +197,8 @@ class HashServer:
         self.max_requests = max_requests_per_batch
         self.max_bytes = max_bytes_in_flight
         device = pool.device.index
-        self.slots = [_Slot(pool, bits, capacity, max_requests_per_batch, device, use_graphs)
-                      for _ in range(slots)]
+        self.slots = [_Slot(pool, bits, capacity, max_requests_per_batch, device, use_graphs,
+                            tune_path) for _ in range(slots)]
         self.queue: collections.deque[Request] = collections.deque()
         self.in_flight_bytes = 0
         self.peak_in_flight_bytes = 0

@@ -73,6 +73,7 @@ def test_null_context_is_rejected_without_cuda(lib):
     assert L.hh_autotune(None, 1 << 30) == hh.HH_ERR_INVALID_ARG
     assert L.hh_tune_save(None, b"x") == hh.HH_ERR_INVALID_ARG
     assert L.hh_tune_describe(None, None, 0) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_set_tune_param(None, b"solo_per_sm", 2) == hh.HH_ERR_INVALID_ARG
 
 
 def test_init_without_a_gpu_reports_no_device(lib):

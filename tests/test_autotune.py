@@ -33,12 +33,12 @@ def test_table_is_well_formed(tuned):
     ctx, before = tuned
     rows = _table(hh.hh_tune_describe(ctx))
     kinds = [r[0] for r in rows]
-    assert kinds == ["fixed"] * 5 + ["ragged", "huge_bucket"]
+    assert kinds == ["fixed"] * 5 + ["ragged", "huge_bucket", "solo_per_sm", "solo_shared"]
     assert [int(r[1]) for r in rows[:5]] == list(range(5))
     assert len(_table(before)) == len(rows)
     # After tuning, the text carries each candidate's measured time.
-    report = [l for l in hh.hh_tune_describe(ctx).splitlines() if l.startswith("# ")]
-    assert len(report) == 7 and all("ms" in l for l in report)
+    report = [l for l in hh.hh_tune_describe(ctx).splitlines() if l.startswith("# ") and "=" in l]
+    assert len(report) == 8 and all("ms" in l for l in report)
 
 
 @pytest.mark.parametrize("length", [0, 17, 64, 200, 1024, 3000, 70000])
@@ -76,7 +76,8 @@ def test_save_and_load_round_trip(tuned, tmp_path):
 
 
 @pytest.mark.parametrize("text", ["fixed 9 128 2 1\n", "fixed 0 100 2 1\n", "ragged 128 9\n",
-                                  "huge_bucket -1\n", "bogus line\n"])
+                                  "huge_bucket -1\n", "solo_per_sm 65\n", "solo_shared 2\n",
+                                  "bogus line\n"])
 def test_bad_table_is_rejected(tmp_path, text):
     path = tmp_path / "bad.txt"
     path.write_text("# libhh tuning table v1\n" + text)
@@ -85,3 +86,20 @@ def test_bad_table_is_rejected(tmp_path, text):
     assert e.value.status == hh.HH_ERR_INVALID_ARG
     with pytest.raises(hh.HHError):
         hh.hh_init(0, str(tmp_path / "missing.txt"))
+
+
+def test_set_tune_param(tmp_path):
+    ctx = hh.hh_init(0)
+    try:
+        hh.hh_set_tune_param(ctx, "solo_per_sm", 2)
+        hh.hh_set_tune_param(ctx, "solo_shared", 0)
+        hh.hh_set_tune_param(ctx, "huge_bucket", 2304)
+        rows = dict((r[0], r[1:]) for r in _table(hh.hh_tune_describe(ctx)))
+        assert rows["solo_per_sm"] == ["2"] and rows["solo_shared"] == ["0"]
+        assert rows["huge_bucket"] == ["2304"]
+        for name, value in (("solo_per_sm", -1), ("solo_shared", 2), ("huge_bucket", 5000),
+                            ("no_such_param", 1)):
+            with pytest.raises(hh.HHError):
+                hh.hh_set_tune_param(ctx, name, value)
+    finally:
+        hh.hh_destroy(ctx)

@@ -336,10 +336,26 @@ def test_segments_shared_key_and_bad_descriptors(ctx):
     assert int(out[7].item()) == 0
 
 
-def test_huge_messages_run_in_thread_pairs(ctx):
-    """Messages of 128 KiB and more take the two-threads-per-message tiles at
-    the head of the length order; mixed with ordinary and short ones, with
-    unaligned starts, every width, against the oracle."""
+@pytest.fixture(scope="module", params=["solo", "pair"])
+def huge_ctx(request, tmp_path_factory):
+    """A context whose huge messages (128 KiB and more) run as solo tiles
+    (one per warp, the default while they are few) or as pair tiles (16 per
+    warp; a tuning table that switches solo tiles off)."""
+    if request.param == "solo":
+        c = hh.hh_init(0)
+    else:
+        path = tmp_path_factory.mktemp("tune") / "pairs.txt"
+        path.write_text("solo_per_sm 0\n")
+        c = hh.hh_init(0, str(path))
+    yield c
+    hh.hh_destroy(c)
+
+
+def test_huge_messages_run_in_solo_and_pair_tiles(huge_ctx):
+    """Messages of 128 KiB and more take the solo or pair tiles at the head of
+    the length order; mixed with ordinary and short ones, with unaligned
+    starts, every width, against the oracle."""
+    ctx = huge_ctx
     g = torch.Generator().manual_seed(91)
     lengths = torch.cat([
         (torch.rand(40, generator=g, dtype=torch.float64) * (4 << 20 - 1)).to(torch.int64) + (1 << 17),
@@ -353,3 +369,34 @@ def test_huge_messages_run_in_thread_pairs(ctx):
         idx = np.unique(np.concatenate([big, np.arange(0, w.n, 7)]))
         assert np.array_equal(got[idx], oracle_hashes(w, bits, indices=idx)), bits
         assert np.array_equal(got, run_ragged(ctx, w, bits, "unsorted"))
+
+
+def test_single_huge_message_alone(huge_ctx):
+    """A batch of one message (sorted too): 2 MiB + 17 bytes starting at an
+    odd offset of its buffer, and one ending on the buffer's last byte."""
+    ctx = huge_ctx
+    for start, length in ((5, (2 << 20) + 17), (0, (1 << 20) + 3)):
+        g = torch.Generator(device=DEV).manual_seed(start + 1)
+        data = torch.randint(0, 256, (start + length,), dtype=torch.uint8, device=DEV, generator=g)
+        offsets = torch.tensor([start, start + length], dtype=torch.int64, device=DEV)
+        keys = torch.tensor([1, -2, 3, -4], dtype=torch.int64, device=DEV)
+        w = workloads.Workload("one", data, offsets, None, keys, False, 1)
+        for bits in (64, 256):
+            got = as_u64(RAGGED_FN[bits](ctx, keys, 0, data, offsets), WORDS[bits])
+            assert hh.hh_get_device_error(ctx) == hh.HH_OK
+            assert np.array_equal(got, oracle_hashes(w, bits)), (start, bits)
+
+
+def test_solo_limit_boundary(ctx):
+    """Exactly 4 huge messages per SM run as solo tiles, one more as pair
+    tiles (the default limit); both agree with the oracle."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for count in (4 * sms, 4 * sms + 1):
+        g = torch.Generator().manual_seed(count)
+        lengths = torch.cat([torch.randint(1 << 17, (1 << 17) + 4096, (count,), generator=g),
+                             torch.randint(0, 3000, (600,), generator=g)])
+        w = workloads.from_lengths(lengths, seed=count, device=DEV, per_message_keys=True)
+        got = run_ragged(ctx, w, 128)
+        idx = np.unique(np.concatenate([np.arange(0, count, 5), [count - 1],
+                                        np.arange(count, w.n, 11)]))
+        assert np.array_equal(got[idx], oracle_hashes(w, 128, indices=idx)), count
