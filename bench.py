@@ -14,6 +14,7 @@ scalar C implementation the tests check against) on the host cores instead.
 from __future__ import annotations
 
 import argparse
+import re
 import concurrent.futures
 import ctypes
 import hashlib
@@ -46,7 +47,7 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=None,
-                   choices=["small", "ragged", "short", "serving"],
+                   choices=["small", "ragged", "short", "serving", "prng", "stats"],
                    help="measure another batch shape instead (one JSON line; not the "
                         "headline step)")
     return p.parse_args()
@@ -137,13 +138,22 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def kernel_source_digest() -> str:
+def kernel_source_digest(unit: str = "hh_fixed.cu") -> str:
+    """Digest of one kernel translation unit and every csrc header it
+    includes (transitively): the sources the DRAM counters were taken on."""
     csrc = os.path.join(ROOT, "paper_1612_06257_gb300", "csrc")
+    seen, todo = [], [unit]
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.exists(os.path.join(csrc, f)):
+            continue
+        seen.append(f)
+        with open(os.path.join(csrc, f)) as fh:
+            todo += re.findall(r'^#include "([^"]+)"', fh.read(), flags=re.M)
     h = hashlib.sha256()
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode() + fh.read())
+    for f in sorted(seen):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 

@@ -286,6 +286,47 @@ int hh_tune_save(hh_ctx* ctx, const char* path);
  * HH_ERR_TOO_LARGE if buf_len is too small (8 KiB always suffices). */
 int hh_tune_describe(hh_ctx* ctx, char* buf, int64_t buf_len);
 
+/*
+ * Counter-mode output (the paper names random-number generation as a use,
+ * Sections 1 and 7): out[i] = HighwayHash-`bits`(key, m_i) for i < n, where
+ * m_i is the 8-byte little-endian encoding of counter0 + i (mod 2^64).
+ * `key`: device uint64[4]; `out`: device uint64[n * bits / 64].  Asynchronous
+ * on `stream`; the same result as hashing those 8-byte messages with
+ * hh_hash*_batch.
+ */
+int hh_prng_fill(hh_ctx* ctx, int bits, const uint64_t* key, uint64_t counter0, int64_t n,
+                 uint64_t* out, void* stream);
+
+/*
+ * Statistical studies (the experiments of Sections 4.3 and 6; not part of
+ * the hash).
+ *
+ * hh_stats_round_table: table[x] = the 64-bit hash, under `key` (HOST
+ * uint64[4]) and with `rounds` (0..16) finalisation rounds instead of 4, of
+ * the nbytes-byte (1..3) little-endian encoding of x, for every x below
+ * 2^(8 nbytes).  `table`: device uint64[2^(8 nbytes)].
+ *
+ * hh_stats_toggle_counts: for a device table of 2^m words (m 1..30), adds to
+ * counts[j * 64 + k] (device uint64[m * 64], zeroed by the caller) the
+ * number of x < 2^m for which bit k of table[x] ^ table[x ^ 2^j] is set.
+ * Every unordered pair is counted twice.
+ *
+ * hh_stats_avalanche: for t < iterations, the message is the first `size`
+ * (1..32) bytes of the little-endian words splitmix64(seed, 4 + 4t + w),
+ * w = 0..3, and the key is splitmix64(seed, 0..3), where splitmix64(s, c)
+ * is output c of Vigna's splitmix64 started at state s.  Adds to
+ * counts[b * 64 + k] (device uint64[8 size * 64], zeroed by the caller) how
+ * many t flip output bit k of the 64-bit hash when input bit b flips.
+ *
+ * All three are asynchronous on `stream`.
+ */
+int hh_stats_round_table(hh_ctx* ctx, const uint64_t* key, int nbytes, int rounds,
+                         uint64_t* table, void* stream);
+int hh_stats_toggle_counts(hh_ctx* ctx, const uint64_t* table, int m, uint64_t* counts,
+                           void* stream);
+int hh_stats_avalanche(hh_ctx* ctx, int size, uint64_t seed, int64_t iterations,
+                       uint64_t* counts, void* stream);
+
 /* Number of kernel launches the last hash call on ctx enqueued. */
 int hh_last_launch_count(hh_ctx* ctx);
 

@@ -11,6 +11,11 @@
            1..4096 messages and one key per request) through the
            continuous-batching server: saturation GB/s, then p50/p99
            latency at Poisson arrival rates swept over 0.1-0.9 of it.
+  prng     2^28 counter-mode 64-bit words (hh_prng_fill): words/s against
+           the integer ceiling (5 Updates per word).
+  stats    the paper's statistical studies on the GPU: toggle bias of all
+           2^24 three-byte inputs after 2, 3 and 4 finalisation rounds, and
+           the avalanche test for sizes 4-32 (49 samples, 1M iterations).
 
 Every input is synthetic and seeded; each workload prints one JSON line.
 """
@@ -23,7 +28,7 @@ import time
 import numpy as np
 import torch
 
-from paper_1612_06257_gb300 import hh, serve, workloads
+from paper_1612_06257_gb300 import hh, serve, stats, workloads
 
 L2_FLUSH_BYTES = 512 << 20
 
@@ -155,7 +160,37 @@ def serving(ctx, dev, requests=64, pool_gib=8, rates=(0.1, 0.3, 0.5, 0.7, 0.9)):
             "sweep": sweep, "device_errors": errors}
 
 
-WORKLOADS = {"small": small, "ragged": ragged, "short": short, "serving": serving}
+def prng(ctx, dev):
+    n = 1 << 28
+    key = workloads.random_u64((4,), workloads.generator(9, dev), dev)
+    out = torch.empty(n, dtype=torch.int64, device=dev)
+    ms, _ = _time(lambda: hh.hh_prng_fill(ctx, 64, key, 12345, n, out=out), 10)
+    ceiling = _update_ceiling(ctx, dev) / 5.0
+    wps = n / (ms / 1e3)
+    return {"workload": "2^28 words, 64-bit, counter-mode (8-byte counters)",
+            "ms": round(ms, 3), "words_per_s": round(wps, 1), "gbps_out": round(n * 8 / ms / 1e6, 1),
+            "integer_ceiling_words_per_s": round(ceiling, 1), "integer_frac": round(wps / ceiling, 4)}
+
+
+def stats_study(ctx, dev):
+    t0 = time.perf_counter()
+    rounds = {}
+    for r in (2, 3, 4):
+        res = stats.round_bias(ctx, r)
+        rounds[r] = {"mean_bias": res["mean_bias"], "max_bias": res["max_bias"]}
+    t1 = time.perf_counter()
+    av = stats.avalanche_study(ctx, iterations=1_000_000)
+    t2 = time.perf_counter()
+    return {"workload": "Section 4.3 round study (all 2^24 3-byte inputs, 24 x 64 bit pairs) and "
+                        "Section 6 avalanche test (sizes 4-32, 49 samples, 1M iterations each)",
+            "bias_definition": "|p - 1/2| per (input bit, output bit) pair",
+            "round_bias": rounds, "round_study_s": round(t1 - t0, 2),
+            "avalanche_median_worst_bias": av["median_worst_bias"], "avalanche_pass_1pct": av["pass"],
+            "avalanche_s": round(t2 - t1, 2)}
+
+
+WORKLOADS = {"small": small, "ragged": ragged, "short": short, "serving": serving, "prng": prng,
+             "stats": stats_study}
 
 
 def run(name: str) -> dict:

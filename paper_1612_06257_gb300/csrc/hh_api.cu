@@ -25,18 +25,7 @@ constexpr int64_t kMaxSortedMessages = 0x7FFFFFFFll;
 constexpr size_t kHostChunkBytes = size_t(64) << 20;  // payload per host-path chunk
 constexpr int64_t kHostChunkMessages = int64_t(1) << 20;
 
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = true;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
+using hh::DeviceGuard;
 
 int to_status(cudaError_t e) {
   if (e == cudaSuccess) return HH_OK;

@@ -49,6 +49,20 @@ struct TuneTable {
 // Read a table written by hh_tune_save; false (t unchanged) on a bad file.
 bool load_tune_table(const char* path, TuneTable& t);
 
+// Makes `dev` the current device for the guard's lifetime.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
 }  // namespace hh
 
 struct hh_ctx {

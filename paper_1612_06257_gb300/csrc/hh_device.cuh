@@ -288,6 +288,17 @@ __device__ __forceinline__ void finalize(State& s) {
   }
 }
 
+// `rounds` rounds of Update(Permute(v0)) (the hash uses 4; other counts
+// serve the study of how many rounds finalisation needs, Section 4.3).
+__device__ __forceinline__ void finalize_rounds(State& s, int rounds) {
+#pragma unroll 1
+  for (int round = 0; round < rounds; ++round) {
+    const uint64_t p[4] = {swap_halves(s.v0[2]), swap_halves(s.v0[3]), swap_halves(s.v0[0]),
+                           swap_halves(s.v0[1])};
+    update(s, p);
+  }
+}
+
 // h[i] = v0[i] + v1[i] + mul0[i] + mul1[i]; the 64-bit hash is h[0], the
 // 128-bit hash h[0..1], the 256-bit hash h[0..3].
 __device__ __forceinline__ void digest(const State& s, uint64_t h[4]) {

@@ -350,7 +350,7 @@ __device__ __forceinline__ unsigned scheduler_slot() {
 }
 
 template <int W, int NST>
-__device__ __noinline__ void solo_tile(const Batch& b, const int32_t* perm, int64_t tile,
+__device__ __forceinline__ void solo_tile(const Batch& b, const int32_t* perm, int64_t tile,
                                           uint8_t* ring, uint32_t ring_s, uintptr_t base,
                                           uintptr_t safe_lo, uintptr_t safe_hi, int lane) {
   constexpr int SW = 8 * W;               // window bytes per stage

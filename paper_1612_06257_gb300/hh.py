@@ -50,7 +50,8 @@ EXPORTS = (
     "hh_hash256_batch", "hh_hash_fixed", "hh_hash_host", "hh_get_device_error",
     "hh_set_kernel", "hh_last_launch_count", "hh_status_string", "hh_set_staged_shape",
     "hh_update_microbench", "hh_hash_batch_noalloc", "hh_hash_segments", "hh_autotune",
-    "hh_tune_save", "hh_tune_describe", "hh_set_tune_param",
+    "hh_tune_save", "hh_tune_describe", "hh_set_tune_param", "hh_prng_fill",
+    "hh_stats_round_table", "hh_stats_toggle_counts", "hh_stats_avalanche",
 )
 
 HH_REGIME_FIXED = 0
@@ -102,6 +103,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.hh_autotune.argtypes = [_vp, _i64]
         L.hh_tune_save.argtypes = [_vp, ctypes.c_char_p]
         L.hh_set_tune_param.argtypes = [_vp, ctypes.c_char_p, _int]
+        L.hh_prng_fill.argtypes = [_vp, _int, _vp, ctypes.c_uint64, _i64, _vp, _vp]
+        L.hh_stats_round_table.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint64), _int, _int,
+                                           _vp, _vp]
+        L.hh_stats_toggle_counts.argtypes = [_vp, _vp, _int, _vp, _vp]
+        L.hh_stats_avalanche.argtypes = [_vp, _int, ctypes.c_uint64, _i64, _vp, _vp]
         L.hh_tune_describe.argtypes = [_vp, ctypes.c_char_p, _i64]
         L.hh_hash_segments.argtypes = [_vp, _int, _vp, ctypes.c_int32, _vp, _vp, _i64, _vp, _vp,
                                        _i64, _vp, _vp, _vp]
@@ -301,6 +307,58 @@ def hh_update_microbench(ctx, variant: int, updates: int, threads: int, out=None
 
 def hh_autotune(ctx, max_device_bytes: int = 1 << 30) -> None:
     _check(load_library().hh_autotune(ctx.ptr, int(max_device_bytes)), "hh_autotune")
+
+
+def hh_prng_fill(ctx, bits, key, counter0: int, n: int, out=None, stream=None):
+    """out[i] = HighwayHash(key, 8-byte LE counter0 + i); returns int64 [n * bits // 64]."""
+    words = {64: 1, 128: 2, 256: 4}.get(int(bits))
+    if words is None:
+        raise ValueError("bits must be 64, 128 or 256")
+    if out is None:
+        out = torch.empty(int(n) * words, dtype=torch.int64, device="cuda:%d" % ctx.device)
+    st = load_library().hh_prng_fill(ctx.ptr, int(bits), _dev_ptr(key, "key", _I64, ctx.device),
+                                     int(counter0) & ((1 << 64) - 1), int(n),
+                                     _dev_ptr(out, "out", _I64, ctx.device),
+                                     _stream_ptr(stream, ctx.device))
+    _check(st, "hh_prng_fill")
+    return out
+
+
+def hh_stats_round_table(ctx, key, nbytes: int, rounds: int, table=None, stream=None):
+    """Hashes of all nbytes-byte inputs with `rounds` finalisation rounds;
+    key: 4 ints (host).  Returns int64 [2 ** (8 * nbytes)]."""
+    if table is None:
+        table = torch.empty(1 << (8 * int(nbytes)), dtype=torch.int64,
+                            device="cuda:%d" % ctx.device)
+    k = (ctypes.c_uint64 * 4)(*[int(x) & ((1 << 64) - 1) for x in key])
+    st = load_library().hh_stats_round_table(ctx.ptr, k, int(nbytes), int(rounds),
+                                             _dev_ptr(table, "table", _I64, ctx.device),
+                                             _stream_ptr(stream, ctx.device))
+    _check(st, "hh_stats_round_table")
+    return table
+
+
+def hh_stats_toggle_counts(ctx, table, m: int, counts=None, stream=None):
+    """Adds toggle counts into counts (int64 [m * 64], zeroed when created here)."""
+    if counts is None:
+        counts = torch.zeros(int(m) * 64, dtype=torch.int64, device="cuda:%d" % ctx.device)
+    st = load_library().hh_stats_toggle_counts(ctx.ptr, _dev_ptr(table, "table", _I64, ctx.device),
+                                               int(m), _dev_ptr(counts, "counts", _I64, ctx.device),
+                                               _stream_ptr(stream, ctx.device))
+    _check(st, "hh_stats_toggle_counts")
+    return counts
+
+
+def hh_stats_avalanche(ctx, size: int, seed: int, iterations: int, counts=None, stream=None):
+    """Adds avalanche flip counts into counts (int64 [8 * size * 64])."""
+    if counts is None:
+        counts = torch.zeros(8 * int(size) * 64, dtype=torch.int64, device="cuda:%d" % ctx.device)
+    st = load_library().hh_stats_avalanche(ctx.ptr, int(size), int(seed) & ((1 << 64) - 1),
+                                           int(iterations),
+                                           _dev_ptr(counts, "counts", _I64, ctx.device),
+                                           _stream_ptr(stream, ctx.device))
+    _check(st, "hh_stats_avalanche")
+    return counts
 
 
 def hh_set_tune_param(ctx, name: str, value: int) -> None:

@@ -74,6 +74,10 @@ def test_null_context_is_rejected_without_cuda(lib):
     assert L.hh_tune_save(None, b"x") == hh.HH_ERR_INVALID_ARG
     assert L.hh_tune_describe(None, None, 0) == hh.HH_ERR_INVALID_ARG
     assert L.hh_set_tune_param(None, b"solo_per_sm", 2) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_prng_fill(None, 64, None, 0, 1, None, None) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_stats_round_table(None, None, 3, 4, None, None) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_stats_toggle_counts(None, None, 24, None, None) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_stats_avalanche(None, 4, 0, 1, None, None) == hh.HH_ERR_INVALID_ARG
 
 
 def test_init_without_a_gpu_reports_no_device(lib):
