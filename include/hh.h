@@ -60,7 +60,8 @@ enum hh_status {
   HH_ERR_TOO_LARGE = 5,     /* a size beyond what the call supports           */
   HH_ERR_BAD_OFFSETS = 6,   /* device: offsets[i+1] < offsets[i] somewhere    */
   HH_ERR_NO_DEVICE = 7,     /* no usable CUDA device with sm_103a             */
-  HH_ERR_BAD_KEY_INDEX = 8  /* device: a key index outside the key table      */
+  HH_ERR_BAD_KEY_INDEX = 8, /* device: a key index outside the key table      */
+  HH_ERR_BAD_CHUNK = 9      /* device: a stream update chunk of 32k+r bytes   */
 };
 
 /* How `keys` is laid out. */
@@ -207,8 +208,8 @@ int hh_hash_batch_noalloc(int bits, const uint64_t* keys, int key_mode, const ui
 
 /*
  * Synchronise `stream`, then return and clear the context's device error
- * word: HH_OK, HH_ERR_BAD_OFFSETS, HH_ERR_BAD_KEY_INDEX or HH_ERR_TIMEOUT
- * (the first one recorded).
+ * word: HH_OK, HH_ERR_BAD_OFFSETS, HH_ERR_BAD_KEY_INDEX, HH_ERR_BAD_CHUNK or
+ * HH_ERR_TIMEOUT (the first one recorded).
  */
 int hh_get_device_error(hh_ctx* ctx, void* stream);
 
@@ -285,6 +286,34 @@ int hh_tune_save(hh_ctx* ctx, const char* path);
  * hh_autotune, by comment lines ('#') with each candidate's measured time;
  * HH_ERR_TOO_LARGE if buf_len is too small (8 KiB always suffices). */
 int hh_tune_describe(hh_ctx* ctx, char* buf, int64_t buf_len);
+
+/*
+ * Streams: n messages that arrive in pieces (Section 4.5 adds the size
+ * only at the end, so everything before the last piece is plain packets).
+ * A stream's state is 16 uint64 words in caller-owned device memory,
+ * states[m * 16 ..]: v0[0..3], v1[0..3], mul0[0..3], mul1[0..3].
+ *
+ * hh_stream_init: states[m] = Init(key of stream m) (key_mode as for
+ * hh_hash*_batch; keys on the device).
+ * hh_stream_update: appends piece m = bytes[offsets[m] .. offsets[m+1]) to
+ * stream m.  Every piece must be a whole number of 32-byte packets (empty
+ * is fine); a piece that is not sets HH_ERR_BAD_CHUNK in the device error
+ * word and leaves that stream's state unchanged.
+ * hh_stream_finish: appends the last piece m (any length), finalises and
+ * writes stream m's `bits`-bit hash to out[m * bits / 64 ..]; the states
+ * are read only.
+ * The hash of a stream equals hh_hash*_batch of the concatenation of its
+ * pieces.  All three are asynchronous on `stream`; the pointers are device
+ * pointers; offsets are non-decreasing.  They run in the length-sorted
+ * warp-tile kernels (HH_KERNEL_AUTO or HH_KERNEL_STAGED_UNSORTED; the naive
+ * and bulk kernels return HH_ERR_INVALID_ARG).
+ */
+int hh_stream_init(hh_ctx* ctx, const uint64_t* keys, int key_mode, int64_t n,
+                   uint64_t* states, void* stream);
+int hh_stream_update(hh_ctx* ctx, uint64_t* states, const uint8_t* bytes, const int64_t* offsets,
+                     int64_t n, void* stream);
+int hh_stream_finish(hh_ctx* ctx, int bits, const uint64_t* states, const uint8_t* bytes,
+                     const int64_t* offsets, int64_t n, uint64_t* out, void* stream);
 
 /*
  * Counter-mode output (the paper names random-number generation as a use,

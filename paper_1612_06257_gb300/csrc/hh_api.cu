@@ -65,6 +65,9 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
   const int64_t n = b.n;
   const bool fixed = b.offsets == nullptr && b.seg_start == nullptr;
 
+  if (b.stream_mode != hh::kWholeMessages &&
+      (ctx->kernel == HH_KERNEL_NAIVE || ctx->kernel == HH_KERNEL_STAGED_BULK))
+    return HH_ERR_INVALID_ARG;  // streams run in the warp-tile and short kernels only
   if (ctx->kernel == HH_KERNEL_NAIVE) {
     ctx->last_launches = 1;
     return to_status(hh::launch_naive(b, stream));
@@ -212,6 +215,7 @@ const char* hh_status_string(int status) {
     case HH_ERR_BAD_OFFSETS: return "offsets decrease";
     case HH_ERR_NO_DEVICE: return "no usable sm_103 CUDA device";
     case HH_ERR_BAD_KEY_INDEX: return "key index outside the key table";
+    case HH_ERR_BAD_CHUNK: return "stream chunk length not a multiple of 32 bytes";
     default: return "unknown status";
   }
 }
@@ -341,6 +345,53 @@ int hh_hash_segments(hh_ctx* ctx, int bits, const uint64_t* key_table, int32_t k
   b.out = out;
   b.words = words;
   return hash_device(ctx, b, static_cast<cudaStream_t>(stream));
+}
+
+int hh_stream_init(hh_ctx* ctx, const uint64_t* keys, int key_mode, int64_t n,
+                   uint64_t* states, void* stream) {
+  if (ctx == nullptr || n < 0 || (key_mode != HH_KEY_SHARED && key_mode != HH_KEY_PER_MESSAGE))
+    return HH_ERR_INVALID_ARG;
+  ctx->last_launches = 0;
+  if (n == 0) return HH_OK;
+  if (keys == nullptr || states == nullptr) return HH_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return HH_ERR_CUDA;
+  ctx->last_launches = 1;
+  return to_status(hh::launch_stream_init(keys, key_mode == HH_KEY_PER_MESSAGE, n, states,
+                                          ctx->num_sms, static_cast<cudaStream_t>(stream)));
+}
+
+// Shared by hh_stream_update and hh_stream_finish.
+static int stream_chunks(hh_ctx* ctx, int mode, int bits, uint64_t* states, const uint8_t* bytes,
+                         const int64_t* offsets, int64_t n, uint64_t* out, void* stream) {
+  if (ctx == nullptr || n < 0) return HH_ERR_INVALID_ARG;
+  const int words = mode == hh::kStreamFinish ? words_of(bits) : 1;
+  if (words == 0) return HH_ERR_INVALID_ARG;
+  ctx->last_launches = 0;
+  if (n == 0) return HH_OK;
+  if (states == nullptr || offsets == nullptr || bytes == nullptr ||
+      (mode == hh::kStreamFinish && out == nullptr))
+    return HH_ERR_INVALID_ARG;
+  hh::Batch b{};
+  b.bytes = bytes;
+  b.offsets = offsets;
+  b.n = n;
+  b.out = out;
+  b.words = words;
+  b.states = states;
+  b.stream_mode = mode;
+  return hash_device(ctx, b, static_cast<cudaStream_t>(stream));
+}
+
+int hh_stream_update(hh_ctx* ctx, uint64_t* states, const uint8_t* bytes, const int64_t* offsets,
+                     int64_t n, void* stream) {
+  return stream_chunks(ctx, hh::kStreamUpdate, 64, states, bytes, offsets, n, nullptr, stream);
+}
+
+int hh_stream_finish(hh_ctx* ctx, int bits, const uint64_t* states, const uint8_t* bytes,
+                     const int64_t* offsets, int64_t n, uint64_t* out, void* stream) {
+  return stream_chunks(ctx, hh::kStreamFinish, bits, const_cast<uint64_t*>(states), bytes,
+                       offsets, n, out, stream);
 }
 
 int hh_hash_host(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,

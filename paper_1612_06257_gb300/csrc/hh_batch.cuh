@@ -29,7 +29,8 @@ __device__ __forceinline__ void resolve_count(Batch& b) {
 // Start (relative to b.bytes) and length of message m.  `bad` is 0, or the
 // error code of an invalid descriptor (decreasing offsets or a segment
 // outside the buffer: kErrBadOffsets; a key index outside the table:
-// kErrBadKey); such a message is hashed as empty and its output is 0.
+// kErrBadKey; a stream-update chunk whose length is not a multiple of 32:
+// kErrBadChunk); such a message is hashed as empty and its output is 0.
 __device__ __forceinline__ void message_bounds(const Batch& b, int64_t m, int64_t& start,
                                                int64_t& len, int& bad) {
   bad = 0;
@@ -53,6 +54,10 @@ __device__ __forceinline__ void message_bounds(const Batch& b, int64_t m, int64_
       bad = kErrBadKey;
       len = 0;
     }
+  }
+  if (b.stream_mode == kStreamUpdate && bad == 0 && (len & 31) != 0) {
+    bad = kErrBadChunk;  // the state is left as it was
+    len = 0;
   }
 }
 

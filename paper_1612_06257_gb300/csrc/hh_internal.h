@@ -11,6 +11,7 @@ namespace hh {
 constexpr int kErrTimeout = 4;
 constexpr int kErrBadOffsets = 6;   // also: a segment outside the buffer
 constexpr int kErrBadKey = 8;       // a key index outside the key table
+constexpr int kErrBadChunk = 9;     // a stream-update chunk not a multiple of 32 bytes
 
 // Length-sort buckets by the number of Updates P = ceil(len / 32) a message
 // needs before finalisation: P itself below 2048, then 128 buckets per
@@ -47,8 +48,17 @@ struct Batch {
   const int64_t* n_dev;      // device word with the message count (<= n), or null
   uint64_t* out;             // words * n
   int words;                 // 1, 2 or 4
+  int stream_mode;           // kWholeMessages, kStreamUpdate or kStreamFinish
   int* err;                  // device error word (first error wins)
+  uint64_t* states;          // streams: n x 16 words (v0, v1, mul0, mul1; lanes 0..3)
 };
+
+// What a batch's messages are: whole messages (Init from the key, hash
+// out); chunks that continue stored stream states (whole 32-byte packets
+// only, state out); or the last chunks of stored streams (hash out).
+constexpr int kWholeMessages = 0;
+constexpr int kStreamUpdate = 1;
+constexpr int kStreamFinish = 2;
 
 // Work-queue state of the staged kernel.
 struct Queue {
@@ -87,6 +97,8 @@ struct StagedShape {
 int blocks_per_sm(const void* kern, int threads, int smem, cudaError_t* err);
 
 cudaError_t launch_naive(const Batch& b, cudaStream_t stream);
+cudaError_t launch_stream_init(const uint64_t* keys, int per_message, int64_t n,
+                               uint64_t* states, int num_sms, cudaStream_t stream);
 cudaError_t launch_staged(const Batch& b, const Queue& q, StagedShape shape, bool aligned16,
                           int num_sms, cudaStream_t stream);
 int staged_blocks_per_sm(StagedShape shape, bool aligned16);

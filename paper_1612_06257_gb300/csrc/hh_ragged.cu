@@ -25,6 +25,7 @@
 #include "hh_device.cuh"
 #include "hh_internal.h"
 #include "hh_ptx.cuh"
+#include "hh_stream.cuh"
 
 namespace hh {
 namespace {
@@ -198,17 +199,13 @@ __device__ __forceinline__ void pair_tile(const Batch& b, const int32_t* perm, i
   const bool valid = idx < last;
   int64_t m = 0, start = 0, len = 0;
   int bad = 0;
-  uint64_t key[4] = {0, 0, 0, 0};
   if (valid) {
     m = static_cast<int64_t>(perm[idx]);
     message_bounds(b, m, start, len, bad);
     if (bad && half == 0) record_error(b.err, bad);
-    const uint64_t* kp = key_of(b, m);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
   }
   Half s;
-  init_half(s, key, half);
+  start_half(b, m, valid, half, s);
   const int64_t my_steps = (len + WP - 1) / WP;
   const int64_t steps = warp_max(my_steps);
   const uintptr_t msg = base + start;
@@ -306,20 +303,7 @@ __device__ __forceinline__ void pair_tile(const Batch& b, const int32_t* perm, i
     buf_read = (buf_read + 1 == NST) ? 0 : buf_read + 1;
   }
   cp_async_wait<0>();
-  finalize_half(s);
-  if (valid) {
-    uint64_t h0 = s.v0[0] + s.v1[0] + s.mul0[0] + s.mul1[0];
-    uint64_t h1 = s.v0[1] + s.v1[1] + s.mul0[1] + s.mul1[1];
-    if (bad) h0 = h1 = 0;
-    uint64_t* o = b.out + m * b.words;
-    if (half == 0) {
-      o[0] = h0;
-      if (b.words >= 2) o[1] = h1;
-    } else if (b.words == 4) {
-      o[2] = h0;
-      o[3] = h1;
-    }
-  }
+  end_half(b, m, valid, bad, half, s);
   __syncwarp();
 }
 
@@ -365,12 +349,8 @@ __device__ __forceinline__ void solo_tile(const Batch& b, const int32_t* perm, i
   int bad = 0;
   message_bounds(b, m, start, len, bad);
   if (bad && lane == 0) record_error(b.err, bad);
-  uint64_t key[4];
-  const uint64_t* kp = key_of(b, m);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
   Half s;
-  init_half(s, key, half);
+  start_half(b, m, true, half, s);
   const int64_t steps = (len + SW - 1) / SW;
   const uintptr_t msg = base + start;
   const uint32_t mis = static_cast<uint32_t>(msg & 15);
@@ -451,20 +431,7 @@ __device__ __forceinline__ void solo_tile(const Batch& b, const int32_t* perm, i
     buf_read = (buf_read + 1 == kSoloStages) ? 0 : buf_read + 1;
   }
   cp_async_wait<0>();
-  finalize_half(s);
-  if (lane < 2) {
-    uint64_t h0 = s.v0[0] + s.v1[0] + s.mul0[0] + s.mul1[0];
-    uint64_t h1 = s.v0[1] + s.v1[1] + s.mul0[1] + s.mul1[1];
-    if (bad) h0 = h1 = 0;
-    uint64_t* o = b.out + m * b.words;
-    if (half == 0) {
-      o[0] = h0;
-      if (b.words >= 2) o[1] = h1;
-    } else if (b.words == 4) {
-      o[2] = h0;
-      o[3] = h1;
-    }
-  }
+  end_half(b, m, lane < 2, bad, half, s);
   __syncwarp();
 }
 
@@ -577,32 +544,16 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
     const bool valid = idx < b.n;
     int64_t m = 0, start = 0, len = 0;
     int bad = 0;
-    uint64_t key[4] = {0, 0, 0, 0};
     if (valid) {
       m = perm ? static_cast<int64_t>(perm[idx]) : idx;
       message_bounds(b, m, start, len, bad);
       if (bad) record_error(b.err, bad);
-      const uint64_t* kp = key_of(b, m);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
     }
     State s;
-    init(s, key);
+    start_state(b, m, valid, s);
     if (__all_sync(kFull, len <= 64)) {
       hash_short(s, base + start, static_cast<uint32_t>(len), base + lo, base + hi);
-      finalize(s);
-      if (valid) {
-        uint64_t h[4];
-        digest(s, h);
-        if (bad) h[0] = h[1] = h[2] = h[3] = 0;
-        uint64_t* o = b.out + m * b.words;
-        o[0] = h[0];
-        if (b.words >= 2) o[1] = h[1];
-        if (b.words == 4) {
-          o[2] = h[2];
-          o[3] = h[3];
-        }
-      }
+      end_state(b, m, valid, bad, s);
       continue;
     }
     const int64_t my_steps = (len + W - 1) / W;
@@ -683,19 +634,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
       buf_read = (buf_read + 1 == NST) ? 0 : buf_read + 1;
     }
     cp_async_wait<0>();
-    finalize(s);
-    if (valid) {
-      uint64_t h[4];
-      digest(s, h);
-      if (bad) h[0] = h[1] = h[2] = h[3] = 0;
-      uint64_t* o = b.out + m * b.words;
-      o[0] = h[0];
-      if (b.words >= 2) o[1] = h[1];
-      if (b.words == 4) {
-        o[2] = h[2];
-        o[3] = h[3];
-      }
-    }
+    end_state(b, m, valid, bad, s);
     __syncwarp();
   }
   // The last warp of a launch with huge messages leaves g_huge_kernels.
@@ -707,6 +646,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
 // Thread per message for batches whose messages are all at most kShortMax
 // bytes, in index order (neighbouring threads read neighbouring bytes), with
 // no shared memory so that occupancy is set by registers alone.
+template <bool kStream>
 __global__ void __launch_bounds__(256) short_kernel(Batch b, const int* run_if) {
   if (run_if != nullptr && *run_if != 0) return;
   resolve_count(b);
@@ -714,7 +654,7 @@ __global__ void __launch_bounds__(256) short_kernel(Batch b, const int* run_if) 
   batch_range(b, lo, hi);
   const uintptr_t base = reinterpret_cast<uintptr_t>(b.bytes);
   uint64_t key[4];
-  const bool shared_key = !b.per_message_keys && b.key_index == nullptr;
+  const bool shared_key = !kStream && !b.per_message_keys && b.key_index == nullptr;
   if (shared_key) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) key[i] = __ldg(b.keys + i);
@@ -727,12 +667,18 @@ __global__ void __launch_bounds__(256) short_kernel(Batch b, const int* run_if) 
     message_bounds(b, m, s0, len, bad);
     if (bad) record_error(b.err, bad);
     len = len < kShortMax ? len : kShortMax;
+    State s;
+    if constexpr (kStream) {
+      start_state(b, m, true, s);
+      hash_short(s, base + s0, static_cast<uint32_t>(len), base + lo, base + hi);
+      end_state(b, m, true, bad, s);
+      continue;
+    }
     if (!shared_key) {
       const uint64_t* kp = key_of(b, m);
 #pragma unroll
       for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
     }
-    State s;
     init(s, key);
     hash_short(s, base + s0, static_cast<uint32_t>(len), base + lo, base + hi);
     finalize(s);
@@ -768,14 +714,15 @@ cudaError_t launch_ragged_t(const Batch& b, const Queue& q, int num_sms, cudaStr
 }  // namespace
 
 cudaError_t launch_short(const Batch& b, const int* run_if, int num_sms, cudaStream_t stream) {
+  auto kern = b.stream_mode != kWholeMessages ? short_kernel<true> : short_kernel<false>;
   cudaError_t e;
-  const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(short_kernel), 256, 0, &e);
+  const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), 256, 0, &e);
   if (e != cudaSuccess) return e;
   const int64_t blocks = (b.n + 255) / 256;
   const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
   const int grid = static_cast<int>(blocks < cap ? blocks : cap);
   if (grid <= 0) return cudaSuccess;
-  short_kernel<<<grid, 256, 0, stream>>>(b, run_if);
+  kern<<<grid, 256, 0, stream>>>(b, run_if);
   return cudaGetLastError();
 }
 

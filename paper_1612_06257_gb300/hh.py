@@ -34,6 +34,7 @@ HH_ERR_TOO_LARGE = 5
 HH_ERR_BAD_OFFSETS = 6
 HH_ERR_NO_DEVICE = 7
 HH_ERR_BAD_KEY_INDEX = 8
+HH_ERR_BAD_CHUNK = 9
 
 HH_KEY_SHARED = 0
 HH_KEY_PER_MESSAGE = 1
@@ -51,7 +52,8 @@ EXPORTS = (
     "hh_set_kernel", "hh_last_launch_count", "hh_status_string", "hh_set_staged_shape",
     "hh_update_microbench", "hh_hash_batch_noalloc", "hh_hash_segments", "hh_autotune",
     "hh_tune_save", "hh_tune_describe", "hh_set_tune_param", "hh_prng_fill",
-    "hh_stats_round_table", "hh_stats_toggle_counts", "hh_stats_avalanche",
+    "hh_stats_round_table", "hh_stats_toggle_counts", "hh_stats_avalanche", "hh_stream_init",
+    "hh_stream_update", "hh_stream_finish",
 )
 
 HH_REGIME_FIXED = 0
@@ -103,6 +105,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.hh_autotune.argtypes = [_vp, _i64]
         L.hh_tune_save.argtypes = [_vp, ctypes.c_char_p]
         L.hh_set_tune_param.argtypes = [_vp, ctypes.c_char_p, _int]
+        L.hh_stream_init.argtypes = [_vp, _vp, _int, _i64, _vp, _vp]
+        L.hh_stream_update.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp]
+        L.hh_stream_finish.argtypes = [_vp, _int, _vp, _vp, _vp, _i64, _vp, _vp]
         L.hh_prng_fill.argtypes = [_vp, _int, _vp, ctypes.c_uint64, _i64, _vp, _vp]
         L.hh_stats_round_table.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint64), _int, _int,
                                            _vp, _vp]
@@ -307,6 +312,47 @@ def hh_update_microbench(ctx, variant: int, updates: int, threads: int, out=None
 
 def hh_autotune(ctx, max_device_bytes: int = 1 << 30) -> None:
     _check(load_library().hh_autotune(ctx.ptr, int(max_device_bytes)), "hh_autotune")
+
+
+def hh_stream_init(ctx, keys, key_mode: int, n: int, states=None, stream=None):
+    """New stream states (int64 [n, 16]) from the keys."""
+    if states is None:
+        states = torch.empty(int(n), 16, dtype=torch.int64, device="cuda:%d" % ctx.device)
+    st = load_library().hh_stream_init(ctx.ptr, _dev_ptr(keys, "keys", _I64, ctx.device),
+                                       int(key_mode), int(n),
+                                       _dev_ptr(states, "states", _I64, ctx.device),
+                                       _stream_ptr(stream, ctx.device))
+    _check(st, "hh_stream_init")
+    return states
+
+
+def hh_stream_update(ctx, states, data, offsets, stream=None):
+    """Append piece m = data[offsets[m]:offsets[m+1]] (whole 32-byte packets) to stream m."""
+    n = offsets.numel() - 1
+    st = load_library().hh_stream_update(ctx.ptr, _dev_ptr(states, "states", _I64, ctx.device),
+                                         _dev_ptr(data, "bytes", (torch.uint8,), ctx.device),
+                                         _dev_ptr(offsets, "offsets", (torch.int64,), ctx.device),
+                                         n, _stream_ptr(stream, ctx.device))
+    _check(st, "hh_stream_update")
+    return states
+
+
+def hh_stream_finish(ctx, bits, states, data, offsets, out=None, stream=None):
+    """Append the last pieces and return the hashes (int64 [n * bits // 64])."""
+    words = {64: 1, 128: 2, 256: 4}.get(int(bits))
+    if words is None:
+        raise ValueError("bits must be 64, 128 or 256")
+    n = offsets.numel() - 1
+    if out is None:
+        out = torch.empty(n * words, dtype=torch.int64, device=data.device)
+    st = load_library().hh_stream_finish(ctx.ptr, int(bits),
+                                         _dev_ptr(states, "states", _I64, ctx.device),
+                                         _dev_ptr(data, "bytes", (torch.uint8,), ctx.device),
+                                         _dev_ptr(offsets, "offsets", (torch.int64,), ctx.device),
+                                         n, _dev_ptr(out, "out", _I64, ctx.device),
+                                         _stream_ptr(stream, ctx.device))
+    _check(st, "hh_stream_finish")
+    return out
 
 
 def hh_prng_fill(ctx, bits, key, counter0: int, n: int, out=None, stream=None):

@@ -48,11 +48,11 @@ def test_library_exports_every_declared_symbol(lib):
 def test_status_strings(lib):
     from paper_1612_06257_gb300 import hh
     seen = set()
-    for code in range(0, 9):
+    for code in range(0, 10):
         s = hh.hh_status_string(code)
         assert s and s != "unknown status"
         seen.add(s)
-    assert len(seen) == 9
+    assert len(seen) == 10
     assert hh.hh_status_string(99) == "unknown status"
 
 
@@ -75,6 +75,9 @@ def test_null_context_is_rejected_without_cuda(lib):
     assert L.hh_tune_describe(None, None, 0) == hh.HH_ERR_INVALID_ARG
     assert L.hh_set_tune_param(None, b"solo_per_sm", 2) == hh.HH_ERR_INVALID_ARG
     assert L.hh_prng_fill(None, 64, None, 0, 1, None, None) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_stream_init(None, None, 0, 1, None, None) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_stream_update(None, None, None, None, 1, None) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_stream_finish(None, 64, None, None, None, 1, None, None) == hh.HH_ERR_INVALID_ARG
     assert L.hh_stats_round_table(None, None, 3, 4, None, None) == hh.HH_ERR_INVALID_ARG
     assert L.hh_stats_toggle_counts(None, None, 24, None, None) == hh.HH_ERR_INVALID_ARG
     assert L.hh_stats_avalanche(None, 4, 0, 1, None, None) == hh.HH_ERR_INVALID_ARG
