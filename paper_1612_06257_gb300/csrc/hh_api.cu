@@ -22,6 +22,8 @@ namespace {
 // sort also finds the long messages that run two threads each.
 constexpr int64_t kSortMinMessages = 1;
 constexpr int64_t kMaxSortedMessages = 0x7FFFFFFFll;
+constexpr int64_t kShortKernelMinMessages = 8192;  // smaller batches: warp-tile kernel only
+constexpr int64_t kFixedRows = 128;                // messages per TMA tile at one per thread
 constexpr size_t kHostChunkBytes = size_t(64) << 20;  // payload per host-path chunk
 constexpr int64_t kHostChunkMessages = int64_t(1) << 20;
 
@@ -73,9 +75,15 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
     return to_status(hh::launch_naive(b, stream));
   }
   if (fixed && b.key_index == nullptr && hh::fixed_tma_supported(b.bytes, b.fixed_len, n)) {
+    hh::StagedShape shape = ctx->tune.fixed[hh::fixed_class(b.fixed_len)];
+    // A batch too small to give every SM a tile is bound by each thread's
+    // Update chain, not by memory: one message per thread (twice the tiles,
+    // half the chain) and 256-byte windows (half the pipeline steps per
+    // message) were fastest for every length measured (256 B to 4 KiB).
+    if (!ctx->tuning && n < static_cast<int64_t>(ctx->num_sms) * kFixedRows * shape.msgs)
+      shape = hh::StagedShape{256, 2, 1};
     ctx->last_launches = 1;
-    return to_status(hh::launch_fixed_tma(b, ctx->tune.fixed[hh::fixed_class(b.fixed_len)],
-                                          ctx->num_sms, stream));
+    return to_status(hh::launch_fixed_tma(b, shape, ctx->num_sms, stream));
   }
 
   const bool sort = !fixed && ctx->kernel != HH_KERNEL_STAGED_UNSORTED && n >= kSortMinMessages;
@@ -103,11 +111,13 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
                            (b.fixed_len % 16 == 0);
     e = hh::launch_staged(b, q, ctx->shape_bulk, aligned16, ctx->num_sms, stream);
   } else {
-    if (sort) {
+    if (sort && n > kShortKernelMinMessages) {
       // All-short batches (the sort's flag says no message is longer than
       // kShortMax) run in the short kernel; otherwise it returns at once and
       // the warp-tile kernel runs.  Both are enqueued, so the sequence of
-      // launches does not depend on the data.
+      // launches does not depend on the data.  Small batches skip the short
+      // kernel: the warp-tile kernel hashes all-short tiles without shared
+      // memory too, and one launch fewer matters more there.
       e = hh::launch_short(b, ctx->d_use_perm, ctx->num_sms, stream);
       if (e != cudaSuccess) return to_status(e);
       ctx->last_launches += 1;

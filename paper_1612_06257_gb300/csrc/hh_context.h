@@ -81,6 +81,7 @@ struct hh_ctx {
   std::string tune_report;  // per-candidate times of the last hh_autotune (comment lines)
   hh::StagedShape shape_bulk{256, 2};  // per-thread bulk-copy kernel
   int last_launches = 0;
+  bool tuning = false;  // hh_autotune is timing shapes: no small-batch override
   // Host-buffer path.
   cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
   hh::HostSlot slots[2];

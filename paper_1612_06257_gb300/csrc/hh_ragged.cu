@@ -682,15 +682,14 @@ __global__ void __launch_bounds__(256) short_kernel(Batch b, const int* run_if) 
     init(s, key);
     hash_short(s, base + s0, static_cast<uint32_t>(len), base + lo, base + hi);
     finalize(s);
-    uint64_t h[4];
-    digest(s, h);
-    if (bad) h[0] = h[1] = h[2] = h[3] = 0;
+    // Only the lanes that are stored are summed (for 64-bit output, one).
+    const uint64_t keep = bad ? 0ull : ~0ull;
     uint64_t* o = b.out + m * b.words;
-    o[0] = h[0];
-    if (b.words >= 2) o[1] = h[1];
+    o[0] = (s.v0[0] + s.v1[0] + s.mul0[0] + s.mul1[0]) & keep;
+    if (b.words >= 2) o[1] = (s.v0[1] + s.v1[1] + s.mul0[1] + s.mul1[1]) & keep;
     if (b.words == 4) {
-      o[2] = h[2];
-      o[3] = h[3];
+      o[2] = (s.v0[2] + s.v1[2] + s.mul0[2] + s.mul1[2]) & keep;
+      o[3] = (s.v0[3] + s.v1[3] + s.mul0[3] + s.mul1[3]) & keep;
     }
   }
 }

@@ -149,6 +149,7 @@ int hh_autotune(hh_ctx* ctx, int64_t max_device_bytes) {
   if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return HH_ERR_CUDA;
   const int saved_kernel = ctx->kernel;
   ctx->kernel = HH_KERNEL_AUTO;
+  ctx->tuning = true;
   const int64_t budget = max_device_bytes & ~int64_t(4095);
   const int64_t max_msgs = int64_t(1) << 22;
   Buffers buf;
@@ -308,6 +309,7 @@ int hh_autotune(hh_ctx* ctx, int64_t max_device_bytes) {
   if (s) cudaStreamDestroy(s);
   ctx->tune_report = status == HH_OK ? report : std::string();
   ctx->kernel = saved_kernel;
+  ctx->tuning = false;
   if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
   return status;
 }
