@@ -273,7 +273,10 @@ int hh_autotune(hh_ctx* ctx, int64_t max_device_bytes);
  *                  default 4);
  *   "solo_shared"  0/1: whether those one-per-warp tiles are also used while
  *                  other launches with such messages are in flight (default
- *                  1).
+ *                  1);
+ *   "fixed_pair"   0/1: whether fixed-length batches too small to give every
+ *                  SM a tile run two threads per message (1, default) or
+ *                  one.
  * HH_ERR_INVALID_ARG for another name or a value out of range.  Results
  * never depend on these settings.
  */

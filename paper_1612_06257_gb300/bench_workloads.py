@@ -79,7 +79,7 @@ def small(ctx, dev):
             "us_per_batch_hot_l2": round(hot * 1e3, 2), "us_per_batch_cold_l2": round(cold * 1e3, 2),
             "gbps_hot": round(w.total_bytes / hot / 1e6, 1),
             "gbps_cold": round(w.total_bytes / cold / 1e6, 1),
-            "note": "4 MiB fits L2; 4096 threads (one message each, 256-byte windows) fill 32 of 152 SMs: a latency regime bound by each thread's Update chain"}
+            "note": "4 MiB fits L2; 4096 messages, two threads each, in 32-row tiles on 128 of 152 SMs: a latency regime bound by each thread's Update chain"}
 
 
 def ragged(ctx, dev):

@@ -75,14 +75,16 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
     return to_status(hh::launch_naive(b, stream));
   }
   if (fixed && b.key_index == nullptr && hh::fixed_tma_supported(b.bytes, b.fixed_len, n)) {
-    hh::StagedShape shape = ctx->tune.fixed[hh::fixed_class(b.fixed_len)];
-    // A batch too small to give every SM a tile is bound by each thread's
-    // Update chain, not by memory: one message per thread (twice the tiles,
-    // half the chain) and 256-byte windows (half the pipeline steps per
-    // message) were fastest for every length measured (256 B to 4 KiB).
-    if (!ctx->tuning && n < static_cast<int64_t>(ctx->num_sms) * kFixedRows * shape.msgs)
-      shape = hh::StagedShape{256, 2, 1};
+    const hh::StagedShape shape = ctx->tune.fixed[hh::fixed_class(b.fixed_len)];
     ctx->last_launches = 1;
+    // A batch too small to give every SM a tile is latency bound: it runs
+    // 256-byte windows, two threads per message (each chain half as long)
+    // or one.
+    if (!ctx->tuning && n < static_cast<int64_t>(ctx->num_sms) * kFixedRows * shape.msgs)
+      return to_status(ctx->tune.fixed_pair
+                           ? hh::launch_fixed_tma_pair(b, ctx->num_sms, stream)
+                           : hh::launch_fixed_tma(b, hh::StagedShape{256, 2, 1}, ctx->num_sms,
+                                                  stream));
     return to_status(hh::launch_fixed_tma(b, shape, ctx->num_sms, stream));
   }
 

@@ -44,6 +44,7 @@ struct TuneTable {
   int huge_bucket = kHugeBucket;  // messages in this bucket and above run two threads each
   int solo_per_sm = kSoloPerSm;   // up to this many huge messages per SM: one warp each
   int solo_shared = 1;            // 1: solo tiles also beside other launches in flight
+  int fixed_pair = 1;             // small fixed batches: 1 two threads per message, 0 one
 };
 
 // Read a table written by hh_tune_save; false (t unchanged) on a bad file.

@@ -206,6 +206,149 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
   }
 }
 
+// Two threads per message, for batches too small to fill the GPU: threads
+// 2r and 2r + 1 keep lane pairs (0, 1) and (2, 3) of row r's state (Update
+// mixes lanes only within a pair), so each thread's Update chain is half
+// as long; they trade v0 in finalisation.  Tiles of ROWS messages (32, 64
+// or 128: the launcher picks the largest that still gives every SM a tile)
+// with the same windows and full/empty barrier protocol as fixed_tma_kernel.
+template <int W, int NST, int ROWS>
+struct PairLayout {
+  static constexpr int kBoxBytes = 128 * ROWS;
+  static constexpr int kStageBytes = W * ROWS;
+  static constexpr int kBarOffset = NST * kStageBytes;
+  static constexpr int kBytes = kBarOffset + 2 * NST * 8 + 1024;  // + alignment slack
+};
+
+template <int W, int NST, int ROWS>
+__global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
+    const __grid_constant__ CUtensorMap tmap, FixedParams p) {
+  using L = PairLayout<W, NST, ROWS>;
+  constexpr int kBoxes = W / 128;
+  constexpr int kWarps = 2 * ROWS / 32;
+  constexpr int kBoxB = L::kBoxBytes;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kBarOffset);
+  uint64_t* empty = full + NST;
+
+  const int t = threadIdx.x, lane = t & 31, row = t >> 1, half = t & 1;
+  const int64_t steps = (p.len + W - 1) / W;
+  const int64_t tiles = (p.n + ROWS - 1) / ROWS;
+  const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t total = my_tiles * steps;
+
+  if (t == 0) {
+    prefetch_tensormap(&tmap);
+    for (int i = 0; i < NST; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kWarps);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  int64_t p_tile = blockIdx.x, p_k = 0;
+  int p_buf = 0;
+  auto issue_next = [&]() {
+    mbar_arrive_expect_tx(&full[p_buf], L::kStageBytes);
+#pragma unroll
+    for (int x = 0; x < kBoxes; ++x)
+      tma_load_2d(smem + p_buf * L::kStageBytes + x * kBoxB, &tmap,
+                  static_cast<int32_t>(p_k * W) + 128 * x, static_cast<int32_t>(p_tile * ROWS),
+                  &full[p_buf]);
+    if (++p_k == steps) {
+      p_k = 0;
+      p_tile += gridDim.x;
+    }
+    p_buf = (p_buf + 1 == NST) ? 0 : p_buf + 1;
+  };
+  if (t == 0)
+    for (int64_t g = 0; g < NST && g < total; ++g) issue_next();
+
+  const int64_t packets = p.len >> 5;
+  const uint32_t r = static_cast<uint32_t>(p.len & 31);
+  const int64_t rem_step = r ? (packets * 32) / W : -1;
+  const int rem_off = r ? static_cast<int>(packets * 32 - rem_step * W) : 0;
+  uint64_t key[4];
+  if (!p.per_message_keys) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) key[i] = __ldg(p.keys + i);
+  }
+  Half s;
+  bool ok = true;
+  int b = 0;
+  uint32_t parity = 0;
+  int64_t g = 0;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t m = tile * ROWS + row;
+    if (p.per_message_keys) {
+      const uint64_t* kp = p.keys + 4 * (m < p.n ? m : 0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) key[q] = __ldg(kp + q);
+    }
+    init_half(s, key, half);
+    for (int64_t k = 0; k < steps; ++k, ++g) {
+      if (ok && !mbar_wait_bounded(&full[b], parity, kWaitLimitNs)) {
+        ok = false;
+        record_error(p.err, kErrTimeout);
+      }
+      const uint8_t* stage = smem + b * L::kStageBytes;
+      if (ok) {
+        const int64_t p0 = k * (W / 32);
+#pragma unroll
+        for (int j = 0; j < W / 32; ++j) {
+          if (p0 + j < packets) {
+            const uint8_t* rp = stage + (j / 4) * kBoxB + row * 128;
+            const uint4 a = lds128(rp + ((((j % 4) * 2 + half) ^ (row & 7)) << 4));
+            update_half(s, join(a.x, a.y), join(a.z, a.w));
+          }
+        }
+        if (k == rem_step) {
+          uint32_t w[8], pk[8];
+          load_swizzled_packet(stage + (rem_off / 128) * kBoxB, row, (rem_off % 128) / 16, w);
+          remainder_packet(r, w, pk);
+          inject_size_half(s, r);
+          if (half == 0) update_half(s, join(pk[0], pk[1]), join(pk[2], pk[3]));
+          else update_half(s, join(pk[4], pk[5]), join(pk[6], pk[7]));
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[b]);
+      if (t == 0 && g + NST < total) {
+        if (!mbar_wait_bounded(&empty[b], parity, kWaitLimitNs)) {
+          record_error(p.err, kErrTimeout);
+        } else {
+          fence_proxy_async_smem();
+          issue_next();
+        }
+      }
+      if (++b == NST) {
+        b = 0;
+        parity ^= 1u;
+      }
+    }
+    finalize_half(s);
+    if (m < p.n) {
+      const uint64_t keep = ok ? ~0ull : 0ull;
+      const uint64_t h0 = (s.v0[0] + s.v1[0] + s.mul0[0] + s.mul1[0]) & keep;
+      const uint64_t h1 = (s.v0[1] + s.v1[1] + s.mul0[1] + s.mul1[1]) & keep;
+      uint64_t* o = p.out + m * p.words;
+      if (half == 0) {
+        o[0] = h0;
+        if (p.words >= 2) o[1] = h1;
+      } else if (p.words == 4) {
+        o[2] = h0;
+        o[3] = h1;
+      }
+    }
+  }
+  if (!ok && t == 0) {
+    for (int i = 0; i < NST; ++i) mbar_wait_bounded(&full[i], 0, kDrainLimitNs);
+  }
+}
+
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                    const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -257,19 +400,45 @@ bool fixed_shape_valid(StagedShape shape) {
   return false;
 }
 
-cudaError_t launch_fixed_tma(const Batch& b, StagedShape shape, int num_sms,
-                             cudaStream_t stream) {
+template <int W, int NST, int ROWS>
+cudaError_t launch_fixed_pair_t(const CUtensorMap& tmap, const FixedParams& p, int num_sms,
+                                cudaStream_t stream) {
+  using L = PairLayout<W, NST, ROWS>;
+  auto kern = fixed_pair_kernel<W, NST, ROWS>;
+  cudaError_t e;
+  const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), 2 * ROWS, L::kBytes, &e);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (p.n + ROWS - 1) / ROWS;
+  const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
+  const int grid = static_cast<int>(tiles < cap ? tiles : cap);
+  kern<<<grid, 2 * ROWS, L::kBytes, stream>>>(tmap, p);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// The batch as a 2D tensor [n][len] of bytes, loaded in `rows`-row x
+// 128-byte boxes with the 128-byte swizzle.
+cudaError_t encode_rows(const Batch& b, CUtensorMap* tmap, int rows) {
   EncodeTiledFn enc = encode_fn();
   if (enc == nullptr) return cudaErrorNotSupported;
-  CUtensorMap tmap;
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(b.fixed_len), static_cast<cuuint64_t>(b.n)};
   const cuuint64_t strides[1] = {static_cast<cuuint64_t>(b.fixed_len)};
-  const cuuint32_t box[2] = {128, kRows};
+  const cuuint32_t box[2] = {128, static_cast<cuuint32_t>(rows)};
   const cuuint32_t elem[2] = {1, 1};
-  CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(b.bytes), dims,
+  CUresult r = enc(tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(b.bytes), dims,
                    strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_fixed_tma(const Batch& b, StagedShape shape, int num_sms,
+                             cudaStream_t stream) {
+  CUtensorMap tmap;
+  cudaError_t e = encode_rows(b, &tmap, kRows);
+  if (e != cudaSuccess) return e;
   FixedParams p{b.n, b.fixed_len, b.keys, b.per_message_keys, b.out, b.words, b.err, 1u};
 #define HH_FIXED(W_, N_, M_)                                          \
   if (shape.window == W_ && shape.stages == N_ && shape.msgs == M_) \
@@ -277,6 +446,20 @@ cudaError_t launch_fixed_tma(const Batch& b, StagedShape shape, int num_sms,
   HH_FIXED_SHAPES(HH_FIXED)
 #undef HH_FIXED
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fixed_tma_pair(const Batch& b, int num_sms, cudaStream_t stream) {
+  // The largest tile height that still gives every SM a tile.
+  const int rows = b.n >= 128 * static_cast<int64_t>(num_sms)  ? 128
+                   : b.n >= 64 * static_cast<int64_t>(num_sms) ? 64
+                                                              : 32;
+  CUtensorMap tmap;
+  cudaError_t e = encode_rows(b, &tmap, rows);
+  if (e != cudaSuccess) return e;
+  FixedParams p{b.n, b.fixed_len, b.keys, b.per_message_keys, b.out, b.words, b.err, 1u};
+  if (rows == 128) return launch_fixed_pair_t<256, 2, 128>(tmap, p, num_sms, stream);
+  if (rows == 64) return launch_fixed_pair_t<256, 2, 64>(tmap, p, num_sms, stream);
+  return launch_fixed_pair_t<256, 2, 32>(tmap, p, num_sms, stream);
 }
 
 }  // namespace hh

@@ -121,6 +121,9 @@ cudaError_t launch_short(const Batch& b, const int* run_if, int num_sms, cudaStr
   X(128, 2, 1) X(128, 3, 1) X(128, 4, 1) X(256, 2, 1) X(256, 3, 1) X(128, 2, 2) X(128, 3, 2)
 bool fixed_tma_supported(const uint8_t* bytes, int64_t len, int64_t n);
 cudaError_t launch_fixed_tma(const Batch& b, StagedShape shape, int num_sms, cudaStream_t stream);
+// Fixed-length batches too small to fill the GPU: two threads per message
+// (one lane pair each), 256-byte windows, two stages.
+cudaError_t launch_fixed_tma_pair(const Batch& b, int num_sms, cudaStream_t stream);
 bool fixed_shape_valid(StagedShape shape);
 
 // Update-rate microbenchmark (threads must be a multiple of 256).

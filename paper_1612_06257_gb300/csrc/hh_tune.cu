@@ -332,6 +332,8 @@ int hh_tune_describe(hh_ctx* ctx, char* buf, int64_t buf_len) {
   text += line;
   std::snprintf(line, sizeof(line), "solo_shared %d\n", ctx->tune.solo_shared);
   text += line;
+  std::snprintf(line, sizeof(line), "fixed_pair %d\n", ctx->tune.fixed_pair);
+  text += line;
   text += ctx->tune_report;
   if (static_cast<int64_t>(text.size()) + 1 > buf_len) return HH_ERR_TOO_LARGE;
   std::memcpy(buf, text.c_str(), text.size() + 1);
@@ -370,6 +372,9 @@ bool set_tune_scalar(TuneTable& t, const char* name, int value) {
   } else if (std::strcmp(name, "solo_shared") == 0) {
     if (value != 0 && value != 1) return false;
     t.solo_shared = value;
+  } else if (std::strcmp(name, "fixed_pair") == 0) {
+    if (value != 0 && value != 1) return false;
+    t.fixed_pair = value;
   } else {
     return false;
   }

@@ -33,7 +33,8 @@ def test_table_is_well_formed(tuned):
     ctx, before = tuned
     rows = _table(hh.hh_tune_describe(ctx))
     kinds = [r[0] for r in rows]
-    assert kinds == ["fixed"] * 5 + ["ragged", "huge_bucket", "solo_per_sm", "solo_shared"]
+    assert kinds == ["fixed"] * 5 + ["ragged", "huge_bucket", "solo_per_sm", "solo_shared",
+                                      "fixed_pair"]
     assert [int(r[1]) for r in rows[:5]] == list(range(5))
     assert len(_table(before)) == len(rows)
     # After tuning, the text carries each candidate's measured time.

@@ -400,3 +400,21 @@ def test_solo_limit_boundary(ctx):
         idx = np.unique(np.concatenate([np.arange(0, count, 5), [count - 1],
                                         np.arange(count, w.n, 11)]))
         assert np.array_equal(got[idx], oracle_hashes(w, 128, indices=idx)), count
+
+
+def test_fixed_batches_either_side_of_the_two_threads_per_message_size(ctx):
+    """Fixed-length batches smaller than one tile per SM (at the tuned
+    messages per thread) run two threads per message in tiles of 32, 64 or
+    128 rows; larger ones run the tuned kernel.  Both sides of the boundary, every width, against the
+    oracle on samples that include both ends of the batch."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    # below: 32-, 64- and 128-row tiles of the two-threads kernel; above: tuned
+    for n in (40 * sms + 3, 80 * sms + 5, 2 * 128 * sms - 1, 2 * 128 * sms + 128):
+        for length, bits in ((48, 256), (1040, 64), (208, 128)):
+            w = workloads.fixed(n, length, seed=n + length, device=DEV,
+                                per_message_keys=(bits == 128))
+            got = as_u64(hh.hh_hash_fixed(ctx, bits, w.keys, w.key_mode, w.data, length, n),
+                         WORDS[bits])
+            assert hh.hh_get_device_error(ctx) == hh.HH_OK
+            idx = np.unique(np.concatenate([np.arange(0, n, 97), [n - 1, n - 2]]))
+            assert np.array_equal(got[idx], oracle_hashes(w, bits, indices=idx)), (n, length)
