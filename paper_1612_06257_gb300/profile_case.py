@@ -5,7 +5,8 @@
 builds one seeded batch on cuda:0 and hashes it `--reps` times through the C
 ABI (the first launch warms up; profile with `-s 1 -c 1` to capture the
 second).  Kinds: fixed (hh_hash_fixed), ragged (log-uniform lengths,
-per-message keys) and short (0..64-byte messages).
+per-message keys), short (0..64-byte messages) and long (n messages of
+`--length` bytes through the offsets form: solo or pair tiles from 128 KiB).
 """
 import argparse
 
@@ -16,7 +17,7 @@ from paper_1612_06257_gb300 import hh, workloads
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("--kind", choices=["fixed", "ragged", "short"], default="fixed")
+    p.add_argument("--kind", choices=["fixed", "ragged", "short", "long"], default="fixed")
     p.add_argument("--n", type=int, default=1 << 18)
     p.add_argument("--length", type=int, default=1024)
     p.add_argument("--bits", type=int, default=64)
@@ -30,6 +31,8 @@ def main():
         w = workloads.fixed(a.n, a.length, seed=1, device=dev)
     elif a.kind == "ragged":
         w = workloads.ragged(a.n, seed=1, device=dev)
+    elif a.kind == "long":
+        w = workloads.from_lengths([a.length] * a.n, seed=1, device=dev)
     else:
         w = workloads.short(a.n, seed=1, device=dev)
     out = torch.empty(w.n * a.bits // 64, dtype=torch.int64, device=dev)
