@@ -110,13 +110,15 @@ __device__ __forceinline__ void hash_step(State& s, const uint8_t* row, uint32_t
 // len < 32(u + 1)), so a warp runs at most two, whatever its length mix.
 // [lo_b, hi_b) is the batch's byte range: words that cross its ends are read
 // bytewise so that no load leaves it.
-__device__ __forceinline__ void hash_short(State& s, uintptr_t msg, uint32_t len, uintptr_t lo_b,
-                                           uintptr_t hi_b) {
+//
+// load_short_words reads the words into x[17]; hash_short_words hashes them
+// (b = msg & 3); hash_short does both.
+__device__ __forceinline__ void load_short_words(uint32_t x[17], uintptr_t msg, uint32_t len,
+                                                 uintptr_t lo_b, uintptr_t hi_b) {
   const uintptr_t w0 = msg & ~uintptr_t(3);
   const uint32_t b = static_cast<uint32_t>(msg & 3);
   const uint32_t nwords = (b + len + 3) >> 2;  // <= 17
   const uintptr_t lo4 = (lo_b + 3) & ~uintptr_t(3), hi4 = hi_b & ~uintptr_t(3);
-  uint32_t x[17];
   if (w0 >= lo4 && w0 + 68 <= hi4) {
     // All 17 words lie inside the batch: load them without per-word tests
     // (words past the message are ignored below).
@@ -139,6 +141,10 @@ __device__ __forceinline__ void hash_short(State& s, uintptr_t msg, uint32_t len
       x[i] = v;
     }
   }
+}
+
+__device__ __forceinline__ void hash_short_words(State& s, const uint32_t x[17], uint32_t b,
+                                                 uint32_t len) {
   const uint32_t sel = 0x3210u + 0x1111u * b;
   uint32_t sw[16];
 #pragma unroll
@@ -158,6 +164,13 @@ __device__ __forceinline__ void hash_short(State& s, uintptr_t msg, uint32_t len
       update_words(s, pkt);
     }
   }
+}
+
+__device__ __forceinline__ void hash_short(State& s, uintptr_t msg, uint32_t len, uintptr_t lo_b,
+                                           uintptr_t hi_b) {
+  uint32_t x[17];
+  load_short_words(x, msg, len, lo_b, hi_b);
+  hash_short_words(s, x, static_cast<uint32_t>(msg & 3), len);
 }
 
 // Half of a 32-byte packet: the 16 bytes at byte `off` of a row, as two
@@ -309,7 +322,8 @@ __device__ __forceinline__ void pair_tile(const Batch& b, const int32_t* perm, i
 
 // One solo tile: a single message of the huge prefix owns the whole warp.
 // Lanes 0 and 1 hash it (one lane pair each, as in a pair tile); all 32
-// lanes copy it.  The warp's ring is re-cut into kSoloStages stages of 8W
+// lanes copy it, and realign each stage in shared memory when the message
+// does not start on a 16-byte boundary.  The warp's ring is re-cut into kSoloStages stages of 8W
 // bytes, so about 14 KiB (W = 256) of the message is in flight and the
 // copies never hold up the Update chain, which then runs at the rate one
 // warp issues it.  Used while the huge messages are few enough to get a
@@ -399,28 +413,40 @@ __device__ __forceinline__ void solo_tile(const Batch& b, const int32_t* perm, i
     buf_issue = (buf_issue + 1 == kSoloStages) ? 0 : buf_issue + 1;
     cp_async_wait<kSoloStages - 1>();
     __syncwarp();
+    uint8_t* row = ring + buf_read * kRow;
+    if (mis != 0) {
+      // All 32 lanes shift the stage left by `mis` bytes in place, so the
+      // two hashing lanes read aligned 16-byte words.  Lane i makes output
+      // words i, i + 32, ... (consecutive lanes touch consecutive words: no
+      // bank conflicts), each from two input words and one PRMT; every lane
+      // reads before any lane writes.  Reads stay inside the row (its 16
+      // slack bytes cover the shift); bytes past the window are never hashed.
+      constexpr int kPerLane = SW / 4 / 32;
+      const uint32_t q = mis >> 2;
+      const uint32_t sel = 0x3210u + 0x1111u * (mis & 3u);
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(row) + q;
+      uint32_t y[kPerLane];
+#pragma unroll
+      for (int j = 0; j < kPerLane; ++j)
+        y[j] = __byte_perm(src[lane + 32 * j], src[lane + 32 * j + 1], sel);
+      __syncwarp();
+      uint32_t* dst = reinterpret_cast<uint32_t*>(row);
+#pragma unroll
+      for (int j = 0; j < kPerLane; ++j) dst[lane + 32 * j] = y[j];
+      __syncwarp();
+    }
     if (lane < 2) {
-      const uint8_t* row = ring + buf_read * kRow;
       const int64_t left = packets - k * (SW / 32);
       const int count = left < SW / 32 ? static_cast<int>(left) : SW / 32;
-      if (mis == 0) {
 #pragma unroll 4
-        for (int j = 0; j < count; ++j) {
-          uint64_t x0, x1;
-          read_half_packet<true>(row, 32u * j + 16u * half, x0, x1);
-          update_half(s, x0, x1);
-        }
-      } else {
-#pragma unroll 4
-        for (int j = 0; j < count; ++j) {
-          uint64_t x0, x1;
-          read_half_packet<false>(row, mis + 32u * j + 16u * half, x0, x1);
-          update_half(s, x0, x1);
-        }
+      for (int j = 0; j < count; ++j) {
+        uint64_t x0, x1;
+        read_half_packet<true>(row, 32u * j + 16u * half, x0, x1);
+        update_half(s, x0, x1);
       }
       if (k == rem_step) {
         uint32_t w[8], rp[8];
-        read_packet<false>(row, mis + static_cast<uint32_t>(packets * 32 - k * SW), w);
+        read_packet<true>(row, static_cast<uint32_t>(packets * 32 - k * SW), w);
         remainder_packet(r, w, rp);
         inject_size_half(s, r);
         if (half == 0) update_half(s, join(rp[0], rp[1]), join(rp[2], rp[3]));
