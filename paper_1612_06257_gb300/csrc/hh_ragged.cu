@@ -283,12 +283,29 @@ __device__ __forceinline__ void pair_tile(const Batch& b, const int32_t* perm, i
     buf_issue = (buf_issue + 1 == NST) ? 0 : buf_issue + 1;
     cp_async_wait<NST - 1>();
     __syncwarp();
+    const int64_t left = packets - k * (WP / 32);
+    // Every message of the tile has a full window: constant trip count.
+    const bool full = __all_sync(kFull, !valid || left >= WP / 32);
     if (k < my_steps) {
       const uint8_t* row = ring + buf_read * L::kStageBytes + slot * kRowStride;
-      const int64_t p0 = k * (WP / 32);
-      const int64_t left = packets - p0;
       const int count = left < WP / 32 ? static_cast<int>(left) : WP / 32;
-      if (aligned) {
+      if (full && aligned) {
+        const uint8_t* hrow = row + 16u * half;
+#pragma unroll
+        for (int j = 0; j < WP / 32; ++j) {
+          uint64_t x0, x1;
+          read_half_packet<true>(hrow, 32u * j, x0, x1);
+          update_half(s, x0, x1);
+        }
+      } else if (full) {
+        const uint32_t off = mis + 16u * half;
+#pragma unroll
+        for (int j = 0; j < WP / 32; ++j) {
+          uint64_t x0, x1;
+          read_half_packet<false>(row, off + 32u * j, x0, x1);
+          update_half(s, x0, x1);
+        }
+      } else if (aligned) {
 #pragma unroll 4
         for (int j = 0; j < count; ++j) {
           uint64_t x0, x1;
@@ -437,12 +454,23 @@ __device__ __forceinline__ void solo_tile(const Batch& b, const int32_t* perm, i
     }
     if (lane < 2) {
       const int64_t left = packets - k * (SW / 32);
-      const int count = left < SW / 32 ? static_cast<int>(left) : SW / 32;
+      if (left >= SW / 32) {
+        // A full stage: constant trip count, offsets fold into the loads.
+        const uint8_t* hrow = row + 16u * half;
+#pragma unroll 16
+        for (int j = 0; j < SW / 32; ++j) {
+          uint64_t x0, x1;
+          read_half_packet<true>(hrow, 32u * j, x0, x1);
+          update_half(s, x0, x1);
+        }
+      } else {
+        const int count = static_cast<int>(left);
 #pragma unroll 4
-      for (int j = 0; j < count; ++j) {
-        uint64_t x0, x1;
-        read_half_packet<true>(row, 32u * j + 16u * half, x0, x1);
-        update_half(s, x0, x1);
+        for (int j = 0; j < count; ++j) {
+          uint64_t x0, x1;
+          read_half_packet<true>(row, 32u * j + 16u * half, x0, x1);
+          update_half(s, x0, x1);
+        }
       }
       if (k == rem_step) {
         uint32_t w[8], rp[8];
