@@ -238,14 +238,14 @@ int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages,
  * ceiling the integer pipes put on Section 4.2's Update).  Each of `threads`
  * threads (a multiple of 32; of 256 when above 256) runs `updates` Updates
  * on register state with no memory traffic and writes one word to
- * out[thread] (device uint64 [threads]).  Variants 0..4 keep the whole
- * four-lane state in one thread and split the 64-bit adds differently
- * between the ALU and FMA pipes; variants 5..9 are the same five splits for
+ * out[thread] (device uint64 [threads]).  Variants 0..5 keep the whole
+ * four-lane state in one thread and split the additions differently
+ * between the ALU and FMA pipes; variants 6..11 are the same six splits for
  * one lane pair per thread (how messages of 128 KiB and more run).  The
  * variants of each group give identical output words.  With few threads it
  * measures the time of one Update chain rather than the pipes' throughput.
  */
-#define HH_UPDATE_VARIANTS 10
+#define HH_UPDATE_VARIANTS 12
 int hh_update_microbench(hh_ctx* ctx, int variant, int64_t updates, int64_t threads,
                          uint64_t* out, void* stream);
 

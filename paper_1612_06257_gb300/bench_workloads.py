@@ -100,11 +100,15 @@ def ragged(ctx, dev):
 
 
 def _update_ceiling(ctx, dev):
-    """Updates per second of the integer-issue microbenchmark (no memory)."""
+    """Updates per second of the integer-issue microbenchmark (no memory):
+    the best of the whole-state variants 1 and 5."""
     threads, updates = 152 * 1024 * 4, 1024
-    out = hh.hh_update_microbench(ctx, 1, updates, threads)
-    ms, _ = _time(lambda: hh.hh_update_microbench(ctx, 1, updates, threads, out=out), 5)
-    return threads * updates / (ms / 1e3)
+    best = 0.0
+    for variant in (1, 5):
+        out = hh.hh_update_microbench(ctx, variant, updates, threads)
+        ms, _ = _time(lambda: hh.hh_update_microbench(ctx, variant, updates, threads, out=out), 5)
+        best = max(best, threads * updates / (ms / 1e3))
+    return best
 
 
 def short(ctx, dev):

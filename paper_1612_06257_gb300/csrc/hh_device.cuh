@@ -113,6 +113,7 @@ __device__ __forceinline__ void zipper_pair(uint64_t a, uint64_t b, uint64_t& za
 //   2: as 1, and v1 += ZM(v0) on the FMA pipe.
 //   3: v0 += mul1 on the ALU, v0 += ZM(v1) and v1 += ZM(v0) on the FMA pipe.
 //   4: as 3, and v1 += packet + mul0 on the FMA pipe as well.
+//   5: as 1, with the 32-bit lo(v0 + mul1) as a multiply-add on the FMA pipe.
 template <int V, int N>
 __device__ __forceinline__ void update_lanes(uint64_t (&v0)[N], uint64_t (&v1)[N],
                                              uint64_t (&mul0)[N], uint64_t (&mul1)[N],
@@ -131,17 +132,22 @@ __device__ __forceinline__ void update_lanes(uint64_t (&v0)[N], uint64_t (&v1)[N
 #pragma unroll
     for (int i = 0; i < N; i += 2) zipper_add_pair(v1[i], v1[i + 1], v0[i], v0[i + 1]);
   } else {
-    // V 1-2: add[i] = mul1 before its update (v0 + add + ZM(v1) is one
-    // 3-input add later).  V 3-4: add[i] = v0 + mul1, formed now.
+    // V 1, 2, 5: add[i] = mul1 before its update (v0 + add + ZM(v1) is
+    // one 3-input add later).  V 3-4: add[i] = v0 + mul1, formed now.
     uint64_t add[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       if (V == 4) v1[i] = add_on_fma(add_on_fma(v1[i], p[i], one), mul0[i], one);
       else v1[i] += p[i] + mul0[i];
       mul0[i] ^= mul_lo(v1[i], v0[i] >> 32);
-      if (V >= 3) {
+      if (V == 3 || V == 4) {
         add[i] = v0[i] + mul1[i];
         mul1[i] ^= mul_lo(add[i], v1[i] >> 32);
+      } else if (V == 5) {
+        add[i] = mul1[i];
+        uint32_t lo;  // lo(v0 + mul1) = lo(v0) * one + lo(mul1)
+        asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(lo) : "r"(lo32(v0[i])), "r"(one), "r"(lo32(add[i])));
+        mul1[i] ^= static_cast<uint64_t>(lo) * hi32(v1[i]);
       } else {
         add[i] = mul1[i];
         const uint32_t lo = lo32(v0[i]) + lo32(add[i]);  // lo(v0 + mul1)
@@ -153,11 +159,12 @@ __device__ __forceinline__ void update_lanes(uint64_t (&v0)[N], uint64_t (&v1)[N
     for (int i = 0; i < N; i += 2) zipper_pair(v1[i], v1[i + 1], z[i], z[i + 1]);
 #pragma unroll
     for (int i = 0; i < N; ++i)
-      v0[i] = (V >= 3) ? add_on_fma(add[i], z[i], one) : v0[i] + add[i] + z[i];
+      v0[i] = (V >= 3 && V <= 4) ? add_on_fma(add[i], z[i], one) : v0[i] + add[i] + z[i];
 #pragma unroll
     for (int i = 0; i < N; i += 2) zipper_pair(v0[i], v0[i + 1], z[i], z[i + 1]);
 #pragma unroll
-    for (int i = 0; i < N; ++i) v1[i] = (V >= 2) ? add_on_fma(v1[i], z[i], one) : v1[i] + z[i];
+    for (int i = 0; i < N; ++i)
+      v1[i] = (V >= 2 && V <= 4) ? add_on_fma(v1[i], z[i], one) : v1[i] + z[i];
   }
 }
 
@@ -167,8 +174,10 @@ __device__ __forceinline__ void update_v(State& s, const uint64_t (&p)[4], uint3
 }
 
 // The variant every kernel uses: fastest in the Update-rate microbenchmark on
-// GB300 (all ALU; moving adds to IMAD.WIDE was slower).
-constexpr int kFastUpdate = 1;
+// GB300.  One 32-bit add on the FMA pipe gains 1.5% (whole state) and 3% (a
+// lane pair) over the all-ALU variant 1; moving the 64-bit adds to
+// IMAD.WIDE (variants 2-4) was slower.
+constexpr int kFastUpdate = 5;
 
 __device__ __forceinline__ void update(State& s, const uint64_t (&p)[4]) {
   update_v<kFastUpdate>(s, p, 1u);

@@ -58,11 +58,13 @@ cudaError_t launch_update_microbench(int variant, int64_t updates, int64_t threa
     case 2: update_rate_kernel<2><<<grid, block, 0, stream>>>(updates, 1u, out); break;
     case 3: update_rate_kernel<3><<<grid, block, 0, stream>>>(updates, 1u, out); break;
     case 4: update_rate_kernel<4><<<grid, block, 0, stream>>>(updates, 1u, out); break;
-    case 5: update_rate_half_kernel<0><<<grid, block, 0, stream>>>(updates, 1u, out); break;
-    case 6: update_rate_half_kernel<1><<<grid, block, 0, stream>>>(updates, 1u, out); break;
-    case 7: update_rate_half_kernel<2><<<grid, block, 0, stream>>>(updates, 1u, out); break;
-    case 8: update_rate_half_kernel<3><<<grid, block, 0, stream>>>(updates, 1u, out); break;
-    case 9: update_rate_half_kernel<4><<<grid, block, 0, stream>>>(updates, 1u, out); break;
+    case 5: update_rate_kernel<5><<<grid, block, 0, stream>>>(updates, 1u, out); break;
+    case 6: update_rate_half_kernel<0><<<grid, block, 0, stream>>>(updates, 1u, out); break;
+    case 7: update_rate_half_kernel<1><<<grid, block, 0, stream>>>(updates, 1u, out); break;
+    case 8: update_rate_half_kernel<2><<<grid, block, 0, stream>>>(updates, 1u, out); break;
+    case 9: update_rate_half_kernel<3><<<grid, block, 0, stream>>>(updates, 1u, out); break;
+    case 10: update_rate_half_kernel<4><<<grid, block, 0, stream>>>(updates, 1u, out); break;
+    case 11: update_rate_half_kernel<5><<<grid, block, 0, stream>>>(updates, 1u, out); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
