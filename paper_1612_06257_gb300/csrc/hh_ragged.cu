@@ -105,9 +105,10 @@ __device__ __forceinline__ void hash_step(State& s, const uint8_t* row, uint32_t
 
 // Messages of at most 64 bytes (a whole warp of them), read straight from
 // global memory: at most 17 aligned 32-bit words per message, shifted into
-// place with one PRMT per word.  Each message needs at most two data Updates
-// (update u exists when len > 32u; it is the padded remainder packet when
-// len < 32(u + 1)), so a warp runs at most two, whatever its length mix.
+// place with one PRMT per word.  A message has at most two data Updates: a
+// whole first packet when len > 32, then its last packet (padded when
+// len mod 32 != 0).  So a warp runs at most two, whatever its length mix,
+// and the padded packet is built once per message.
 // [lo_b, hi_b) is the batch's byte range: words that cross its ends are read
 // bytewise so that no load leaves it.
 //
@@ -143,26 +144,42 @@ __device__ __forceinline__ void load_short_words(uint32_t x[17], uintptr_t msg, 
   }
 }
 
+// The last packet of a message from the eight words t that hold its last
+// len mod 32 (= r) bytes, padded as Section 4.5 asks: whole 4-byte groups
+// stay in place, the final r mod 4 bytes go to bytes 28.., the rest is zero.
+// r == 0 leaves the whole packet t.
+__device__ __forceinline__ void last_packet(uint32_t r, const uint32_t t[8], uint32_t pkt[8]) {
+  const uint32_t whole = r ? (r >> 2) : 8u;
+  // t[whole] for whole < 8, as a three-level select (no run-time index).
+  const uint32_t w01 = (whole & 1u) ? t[1] : t[0], w23 = (whole & 1u) ? t[3] : t[2];
+  const uint32_t w45 = (whole & 1u) ? t[5] : t[4], w67 = (whole & 1u) ? t[7] : t[6];
+  const uint32_t w03 = (whole & 2u) ? w23 : w01, w47 = (whole & 2u) ? w67 : w45;
+  const uint32_t last = (whole & 4u) ? w47 : w03;
+  const uint32_t keep_last = (1u << (8u * (r & 3u))) - 1u;  // 0 when r mod 4 == 0
+#pragma unroll
+  for (int j = 0; j < 8; ++j) pkt[j] = (static_cast<uint32_t>(j) < whole) ? t[j] : 0u;
+  pkt[7] |= last & keep_last;
+}
+
 __device__ __forceinline__ void hash_short_words(State& s, const uint32_t x[17], uint32_t b,
                                                  uint32_t len) {
   const uint32_t sel = 0x3210u + 0x1111u * b;
   uint32_t sw[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) sw[j] = __byte_perm(x[j], x[j + 1], sel);
+  const bool two = len > 32u;  // a whole packet precedes the last one
+  const uint32_t r = len & 31u;
+  uint32_t t[8], last[8];
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    if (len > 32u * u) {
-      const bool partial = len < 32u * (u + 1);
-      const uint32_t r = partial ? len - 32u * u : 0u;
-      if (partial) inject_size(s, r);
-      uint32_t tail[8], rp[8], pkt[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) tail[j] = sw[8 * u + j];
-      remainder_packet(r, tail, rp);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) pkt[j] = partial ? rp[j] : tail[j];
-      update_words(s, pkt);
-    }
+  for (int j = 0; j < 8; ++j) t[j] = two ? sw[8 + j] : sw[j];
+  last_packet(r, t, last);
+  if (two) {
+    const uint32_t* first = sw;
+    update_words(s, first);
+  }
+  if (len != 0u) {
+    inject_size(s, r);  // a size of 0 changes nothing
+    update_words(s, last);
   }
 }
 
