@@ -13,6 +13,9 @@
 // shuffle, and chunk offsets fold into the instruction's immediate.  Only
 // the (at most two) partial 16-byte blocks at the two ends of the whole
 // batch are read bytewise, so no load leaves [offsets[0], offsets[n]).
+// When every row's window lies inside its message and its aligned span
+// inside the batch (all but the last window of long messages), the rows copy
+// all their chunks with no per-chunk tests.
 //
 // Reading a packet: when every message of the warp tile starts 16-byte
 // aligned, two 128-bit shared loads; otherwise nine 32-bit loads from the
@@ -638,6 +641,28 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
 
     // Stage k of all 32 rows into ring buffer (k % NST).
     auto issue = [&](int64_t k, int buf) {
+      // When every row's window lies inside its message and the row's whole
+      // 16-byte aligned span inside the batch, all rows copy every chunk
+      // (bytes past a window land in the row's slack and are never hashed).
+      const uintptr_t a0_full = (msg + static_cast<uintptr_t>(k) * W) & ~uintptr_t(15);
+      const bool row_full = k < my_steps && (k + 1) * W <= len && a0_full >= safe_lo &&
+                            a0_full + L::kStride <= safe_hi;
+      if (__all_sync(kFull, row_full)) {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int row = 8 * h + row_in_pass;
+          const uintptr_t rbase = static_cast<uintptr_t>(
+              __shfl_sync(kFull, static_cast<unsigned long long>(a0_full), row));
+          const char* src = reinterpret_cast<const char*>(rbase) + 16 * part;
+          const uint32_t dst = ring_s + buf * L::kStageBytes + row * L::kStride + 16 * part;
+#pragma unroll
+          for (int i = 0; i < L::kPerLane; ++i)
+            if (i + 1 < L::kPerLane || part + 4 * i < L::kChunks)
+              cp_async16(dst + 64 * i, src + 64 * i);
+        }
+        cp_async_commit();
+        return;
+      }
       uint8_t* stage = ring + buf * L::kStageBytes;
       // Owner side: this lane's window, as a 16-byte aligned chunk range.
       uintptr_t a0 = 0;
