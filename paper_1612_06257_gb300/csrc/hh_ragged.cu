@@ -524,7 +524,8 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
   const uintptr_t safe_lo = (base + lo + 15) & ~uintptr_t(15);
   const uintptr_t safe_hi = (base + hi) & ~uintptr_t(15);
 
-  // Copy roles: lane = 4 * row_in_pass + part; pass h covers rows 8h..8h+7.
+  // Copy roles: lane = 4 * row_in_pass + part; pass h copies the windows of
+  // messages (lanes) 8h..8h+7.
   const int part = lane & 3;
   const int row_in_pass = lane >> 2;
 
@@ -638,8 +639,27 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
     const int64_t packets = len >> 5;
     const uint32_t r = static_cast<uint32_t>(len & 31);
     const int64_t rem_step = r ? (packets * 32) / W : -1;
+    // This lane's row in each stage.  Rows rotate the banks by 4 words, so
+    // rows q, q + 8, q + 16, q + 24 share four banks, and two of them
+    // conflict on an unaligned 32-bit load when their messages start at the
+    // same word of a 16-byte block.  Ranking the lanes by that word (mis / 4)
+    // and giving rank q row q spreads equal words over the eight groups.
+    int my_row = lane;
+    if (!aligned) {
+      const uint32_t word = valid ? (mis >> 2) : 0u;
+      const unsigned below = (1u << lane) - 1u;
+      int rank = 0;
+#pragma unroll
+      for (uint32_t v = 0; v < 4; ++v) {
+        const unsigned same = __ballot_sync(kFull, word == v);
+        if (v < word) rank += __popc(same);
+        if (v == word) rank += __popc(same & below);
+      }
+      my_row = rank;
+    }
 
-    // Stage k of all 32 rows into ring buffer (k % NST).
+    // Stage k of all 32 messages into ring buffer (k % NST); message `lane`
+    // goes to row my_row.
     auto issue = [&](int64_t k, int buf) {
       // When every row's window lies inside its message and the row's whole
       // 16-byte aligned span inside the batch, all rows copy every chunk
@@ -650,9 +670,10 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
       if (__all_sync(kFull, row_full)) {
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-          const int row = 8 * h + row_in_pass;
+          const int owner = 8 * h + row_in_pass;
           const uintptr_t rbase = static_cast<uintptr_t>(
-              __shfl_sync(kFull, static_cast<unsigned long long>(a0_full), row));
+              __shfl_sync(kFull, static_cast<unsigned long long>(a0_full), owner));
+          const int row = __shfl_sync(kFull, my_row, owner);
           const char* src = reinterpret_cast<const char*>(rbase) + 16 * part;
           const uint32_t dst = ring_s + buf * L::kStageBytes + row * L::kStride + 16 * part;
 #pragma unroll
@@ -683,18 +704,19 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
         range = first | (end << 8);
         if (c0 > gs || c1 < ge || c1 <= c0) {
           // Bytes in the partial blocks at the batch ends: read bytewise.
-          uint8_t* row = stage + lane * L::kStride;
+          uint8_t* row = stage + my_row * L::kStride;
           for (uintptr_t p = gs; p < ge; ++p)
             if (p < c0 || p >= c1 || c1 <= c0) row[p - a0] = *reinterpret_cast<const uint8_t*>(p);
         }
       }
-      // Copier side: four lanes per row, eight rows per pass.
+      // Copier side: four lanes per message, eight messages per pass.
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
-        const int row = 8 * h + row_in_pass;
+        const int owner = 8 * h + row_in_pass;
         const uintptr_t rbase = static_cast<uintptr_t>(
-            __shfl_sync(kFull, static_cast<unsigned long long>(a0), row));
-        const uint32_t rr = __shfl_sync(kFull, range, row);
+            __shfl_sync(kFull, static_cast<unsigned long long>(a0), owner));
+        const uint32_t rr = __shfl_sync(kFull, range, owner);
+        const int row = __shfl_sync(kFull, my_row, owner);
         const uint32_t first = rr & 0xff, end = rr >> 8;
         const char* src = reinterpret_cast<const char*>(rbase) + 16 * part;
         const uint32_t dst = ring_s + buf * L::kStageBytes + row * L::kStride + 16 * part;
@@ -720,7 +742,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
       cp_async_wait<NST - 1>();
       __syncwarp();
       if (k < my_steps) {
-        const uint8_t* row = ring + buf_read * L::kStageBytes + lane * L::kStride;
+        const uint8_t* row = ring + buf_read * L::kStageBytes + my_row * L::kStride;
         if (aligned)  // warp-uniform
           hash_step<W, true>(s, row, 0u, k, packets, r, rem_step, 1u);
         else
