@@ -91,12 +91,32 @@ __device__ __forceinline__ void hash_step(State& s, const uint8_t* row, uint32_t
                                           int64_t packets, uint32_t r, int64_t rem_step,
                                           uint32_t one) {
   const int64_t p0 = k * (W / 32);
+  if (kAligned) {
 #pragma unroll
-  for (int j = 0; j < W / 32; ++j) {
-    if (p0 + j < packets) {
-      uint32_t w[8];
-      read_packet<kAligned>(row, mis + 32u * j, w);
-      update_words_v<kFastUpdate>(s, w, one);
+    for (int j = 0; j < W / 32; ++j) {
+      if (p0 + j < packets) {
+        uint32_t w[8];
+        read_packet<true>(row, 32u * j, w);
+        update_words_v<kFastUpdate>(s, w, one);
+      }
+    }
+  } else {
+    // Consecutive packets share the word that straddles them.
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(row + (mis & ~3u));
+    const uint32_t sel = 0x3210u + 0x1111u * (mis & 3u);
+    uint32_t prev = p[0];
+#pragma unroll
+    for (int j = 0; j < W / 32; ++j) {
+      if (p0 + j < packets) {
+        uint32_t x[8], w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = p[8 * j + 1 + i];
+        w[0] = __byte_perm(prev, x[0], sel);
+#pragma unroll
+        for (int i = 1; i < 8; ++i) w[i] = __byte_perm(x[i - 1], x[i], sel);
+        prev = x[7];
+        update_words_v<kFastUpdate>(s, w, one);
+      }
     }
   }
   if (k == rem_step) {
