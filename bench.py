@@ -6,7 +6,8 @@ uniform random bytes (1 GiB) with one 256-bit key, through libhh's C ABI.
 The inputs (1 GiB) are larger than L2 (129 MB), so no flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --workload small|ragged|short|serving
+  python bench.py --workload small|ragged|short|serving|prng|stats
+  python bench.py --workload oracle      (CPU only: the oracle on one thread)
 
 Rank 0 prints one JSON line.  --impl reference times the CPU oracle (the
 scalar C implementation the tests check against) on the host cores instead.
@@ -47,7 +48,7 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=None,
-                   choices=["small", "ragged", "short", "serving", "prng", "stats"],
+                   choices=["small", "ragged", "short", "serving", "prng", "stats", "oracle"],
                    help="measure another batch shape instead (one JSON line; not the "
                         "headline step)")
     return p.parse_args()
@@ -204,6 +205,73 @@ def cpu_baseline(keys, data, offsets, n_total, target_cpu_s=12.0, max_passes=8):
                       "%.2f s wall, %.1f s CPU" % (n_total, n_total * MESSAGE_BYTES / 2**20, passes,
                                                     cores, total_s, total_s * cores),
             "hashes_per_s": round(passes * n_total / total_s, 1)}, out
+
+
+def host_cpu():
+    """Model name and nominal maximum clock (MHz, or None) of host CPU 0."""
+    model, mhz = "unknown", None
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+        m = re.search(r"^model name\s*:\s*(.+)$", info, flags=re.M)
+        if m:
+            model = m.group(1).strip()
+        else:
+            part = re.search(r"^CPU part\s*:\s*(\S+)$", info, flags=re.M)
+            impl = re.search(r"^CPU implementer\s*:\s*(\S+)$", info, flags=re.M)
+            if part and impl:
+                model = "implementer %s part %s" % (impl.group(1), part.group(1))
+        m = re.search(r"^cpu MHz\s*:\s*([0-9.]+)$", info, flags=re.M)
+        if m:
+            mhz = float(m.group(1))
+    except OSError:
+        pass
+    try:
+        with open("/sys/devices/system/cpu/cpu0/cpufreq/cpuinfo_max_freq") as f:
+            mhz = int(f.read().strip()) / 1000.0
+    except (OSError, ValueError):
+        pass
+    return model, mhz
+
+
+# Section 5, Table 1: HighwayHash with AVX2 on one core of a 2.6 GHz Xeon
+# E5-2690 v3 (cache-resident inputs), cycles per byte by message size.
+PAPER_AVX2_CPB = {8: 7.34, 31: 1.81, 32: 1.71, 63: 1.04, 64: 0.95, 1024: 0.24}
+
+
+def oracle_cycles_table(target_s=0.5):
+    """The oracle as it stands, on ONE host thread, over cache-resident
+    messages of the sizes of Section 5's table: about 64 KiB of messages
+    of one size, hashed again and again for about `target_s` seconds.
+    Cycles per byte use the nominal maximum clock, so they are approximate;
+    the paper's AVX2 figures are context, not a target."""
+    import oracle
+    model, mhz = host_cpu()
+    rng = np.random.default_rng(7)
+    keys = rng.integers(0, 2**63, 4, dtype=np.uint64)
+    rows = []
+    for size in sorted(PAPER_AVX2_CPB):
+        n = max(1, (64 << 10) // size)
+        data = rng.integers(0, 256, n * size, dtype=np.uint8)
+        offsets = np.arange(n + 1, dtype=np.int64) * size
+        out = np.zeros((n, 1), dtype=np.uint64)
+        oracle.hash_batch(keys, False, data, offsets, 64, 0, n, out)
+        reps, t0 = 0, time.perf_counter()
+        while reps == 0 or time.perf_counter() - t0 < target_s:
+            oracle.hash_batch(keys, False, data, offsets, 64, 0, n, out)
+            reps += 1
+        secs = (time.perf_counter() - t0) / (reps * n)
+        row = {"bytes": size, "ns_per_hash": round(secs * 1e9, 2),
+               "gbps": round(size / secs / 1e9, 4), "hashes_per_s": round(1 / secs, 1),
+               "paper_avx2_cycles_per_byte": PAPER_AVX2_CPB[size]}
+        if mhz:
+            row["cycles_per_byte"] = round(secs * mhz * 1e6 / size, 2)
+        rows.append(row)
+    return {"workload": "CPU oracle on one host thread, cache-resident messages of 8..1024 B",
+            "cpu": model, "nominal_mhz": mhz, "threads": 1, "kind": "oracle",
+            "build": "gcc -O2, no architecture flags (scalar C, one 64-bit lane at a time)",
+            "rows": rows, "name": "oracle", "data": "synthetic (seeded, host)",
+            "note": "paper figures: AVX2 on a 2.6 GHz Xeon E5-2690 v3 (Section 5); context only"}
 
 
 # --------------------------------------------------------------- our arm
@@ -409,7 +477,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.workload is not None:
+    if args.workload == "oracle":
+        res = oracle_cycles_table() if rank == 0 else None
+    elif args.workload is not None:
         from paper_1612_06257_gb300 import bench_workloads
         res = bench_workloads.run(args.workload) if rank == 0 else None
     elif args.impl == "reference":

@@ -58,6 +58,17 @@ def _time(fn, reps, flush=None):
     return float(np.median(times)), times
 
 
+def _naive_ms(ctx, fn, reps, flush=None):
+    """Median ms of `fn` with the naive kernel (one thread per message,
+    direct global loads): the speedup baseline on the same GPU."""
+    hh.hh_set_kernel(ctx, hh.HH_KERNEL_NAIVE)
+    try:
+        ms, _ = _time(fn, reps, flush)
+    finally:
+        hh.hh_set_kernel(ctx, hh.HH_KERNEL_AUTO)
+    return ms
+
+
 def small(ctx, dev):
     w = workloads.fixed(4096, 1024, seed=1, device=dev)
     out = torch.empty(w.n, dtype=torch.int64, device=dev)
@@ -75,8 +86,11 @@ def small(ctx, dev):
     torch.cuda.synchronize()
     hot = e0.elapsed_time(e1) / 200
     cold, _ = _time(fn, 50, flush=lambda: junk.fill_(1))
+    naive_cold = _naive_ms(ctx, fn, 50, flush=lambda: junk.fill_(1))
     return {"workload": "4096 x 1024 B, one key, 64-bit (fixed-length batch)",
             "us_per_batch_hot_l2": round(hot * 1e3, 2), "us_per_batch_cold_l2": round(cold * 1e3, 2),
+            "naive_us_per_batch_cold_l2": round(naive_cold * 1e3, 2),
+            "speedup_vs_naive_cold": round(naive_cold / cold, 2),
             "gbps_hot": round(w.total_bytes / hot / 1e6, 1),
             "gbps_cold": round(w.total_bytes / cold / 1e6, 1),
             "note": "4 MiB fits L2; 4096 messages, two threads each, in 32-row tiles on 128 of 152 SMs: a latency regime bound by each thread's Update chain"}
@@ -88,6 +102,7 @@ def ragged(ctx, dev):
     fn = lambda: hh.hh_hash64_batch(ctx, w.keys, 1, w.data, w.offsets, out=out)  # noqa: E731
     ms, _ = _time(fn, 10)
     launches = hh.hh_last_launch_count(ctx)
+    naive = _naive_ms(ctx, fn, 3)
     alg = w.total_bytes + 8 * (w.n + 1) + 32 * w.n + 8 * w.n
     peak, kind = _peak_hbm()
     return {"workload": "2^22 messages, log-uniform lengths in [0, 65536], per-message keys, "
@@ -96,7 +111,9 @@ def ragged(ctx, dev):
             "roofline": {"bound": "hbm", "achieved": round(alg / ms / 1e6, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(alg / ms / 1e6 / peak, 4),
                          "peak_source": kind, "algorithmic_bytes": alg},
-            "launches_per_batch": launches}
+            "launches_per_batch": launches,
+            "naive_gbps": round(w.total_bytes / naive / 1e6, 1),
+            "speedup_vs_naive": round(naive / ms, 2)}
 
 
 def _update_ceiling(ctx, dev):
@@ -126,6 +143,10 @@ def short(ctx, dev):
         res["hashes_per_s_%d" % bits] = round(hps, 1)
         res["integer_frac_%d" % bits] = round(hps / ceiling, 4)
         res["gbps_%d" % bits] = round(w.total_bytes / ms / 1e6, 1)
+        if bits == 64:
+            naive = _naive_ms(ctx, lambda: fn(ctx, w.keys, 0, w.data, w.offsets, out=out), 5)
+            res["naive_hashes_per_s_64"] = round(w.n / (naive / 1e3), 1)
+            res["speedup_vs_naive_64"] = round(naive / ms, 2)
     return res
 
 
