@@ -22,6 +22,7 @@ import hashlib
 import json
 import os
 import statistics
+import subprocess
 import sys
 import threading
 import time
@@ -231,6 +232,18 @@ def host_cpu():
             mhz = int(f.read().strip()) / 1000.0
     except (OSError, ValueError):
         pass
+    if model.startswith("implementer") or mhz is None:
+        # Arm hosts name the core only through lscpu (and may expose no clock).
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            m = re.search(r"^Model name:\s*(.+)$", out, flags=re.M)
+            if m and model.startswith("implementer"):
+                model = m.group(1).strip()
+            m = re.search(r"^CPU max MHz:\s*([0-9.]+)$", out, flags=re.M)
+            if m and mhz is None:
+                mhz = float(m.group(1))
+        except (OSError, ValueError, subprocess.SubprocessError):
+            pass
     return model, mhz
 
 
