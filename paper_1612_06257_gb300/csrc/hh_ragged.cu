@@ -49,6 +49,10 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -782,10 +786,10 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
 }
 
 // Thread per message for batches whose messages are all at most kShortMax
-// bytes, in index order (neighbouring threads read neighbouring bytes), with
-// no shared memory so that occupancy is set by registers alone.
+// bytes, in index order (neighbouring threads read neighbouring bytes).
+// Three blocks of 256 threads per SM (80 registers).
 template <bool kStream>
-__global__ void __launch_bounds__(256) short_kernel(Batch b, const int* run_if) {
+__global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, const int* run_if) {
   if (run_if != nullptr && *run_if != 0) return;
   resolve_count(b);
   int64_t lo, hi;
@@ -798,11 +802,33 @@ __global__ void __launch_bounds__(256) short_kernel(Batch b, const int* run_if) 
     for (int i = 0; i < 4; ++i) key[i] = __ldg(b.keys + i);
   }
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; m < b.n;
-       m += stride) {
+  // Offsets form: each thread's next two offsets are copied into shared
+  // memory one iteration ahead, so that the only global loads a message
+  // waits for are its own words.
+  __shared__ int64_t next_offsets[2][256][2];
+  const bool ahead = !kStream && b.offsets != nullptr && b.key_index == nullptr;
+  int cur = 0;
+  const int64_t first_m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  auto fetch_offsets = [&](int64_t mm, int slot) {
+    cp_async8(smem_u32(&next_offsets[slot][threadIdx.x][0]), b.offsets + mm);
+    cp_async8(smem_u32(&next_offsets[slot][threadIdx.x][1]), b.offsets + mm + 1);
+    cp_async_commit();
+  };
+  if (ahead && first_m < b.n) fetch_offsets(first_m, 0);
+  for (int64_t m = first_m; m < b.n; m += stride) {
     int64_t s0, len;
     int bad;
-    message_bounds(b, m, s0, len, bad);
+    if (ahead) {
+      cp_async_wait<0>();
+      const int64_t s = next_offsets[cur][threadIdx.x][0], e = next_offsets[cur][threadIdx.x][1];
+      if (m + stride < b.n) fetch_offsets(m + stride, cur ^ 1);
+      cur ^= 1;
+      bad = e < s ? kErrBadOffsets : 0;
+      s0 = s;
+      len = bad ? 0 : e - s;
+    } else {
+      message_bounds(b, m, s0, len, bad);
+    }
     if (bad) record_error(b.err, bad);
     len = len < kShortMax ? len : kShortMax;
     State s;
