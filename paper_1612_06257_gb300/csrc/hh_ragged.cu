@@ -49,6 +49,10 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
 }
@@ -215,6 +219,25 @@ __device__ __forceinline__ void hash_short(State& s, uintptr_t msg, uint32_t len
   uint32_t x[17];
   load_short_words(x, msg, len, lo_b, hi_b);
   hash_short_words(s, x, static_cast<uint32_t>(msg & 3), len);
+}
+
+// Starts copying the 17 words that hold a message of at most 64 bytes into
+// a thread's shared-memory slot (slot_s is its shared address), as one
+// cp.async group; words that cross the batch ends are read now, bytewise.
+__device__ __forceinline__ void stage_short_words(uint32_t* slot, uint32_t slot_s, uintptr_t msg,
+                                                  uint32_t len, uintptr_t lo_b, uintptr_t hi_b) {
+  const uintptr_t w0 = msg & ~uintptr_t(3);
+  const uintptr_t lo4 = (lo_b + 3) & ~uintptr_t(3), hi4 = hi_b & ~uintptr_t(3);
+  if (w0 >= lo4 && w0 + 68 <= hi4) {
+#pragma unroll
+    for (int i = 0; i < 17; ++i) cp_async4(slot_s + 4 * i, reinterpret_cast<const uint32_t*>(w0) + i);
+  } else {
+    uint32_t x[17];
+    load_short_words(x, msg, len, lo_b, hi_b);
+#pragma unroll
+    for (int i = 0; i < 17; ++i) slot[i] = x[i];
+  }
+  cp_async_commit();
 }
 
 // Half of a 32-byte packet: the 16 bytes at byte `off` of a row, as two
@@ -785,6 +808,21 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
     atomicSub(&g_huge_kernels, 1u);
 }
 
+// The hash of message m from its finalised state (zero for an invalid
+// descriptor).  Only the lanes that are stored are summed (for 64-bit
+// output, one).
+__device__ __forceinline__ void store_short_hash(const Batch& b, int64_t m, int bad,
+                                                 const State& s) {
+  const uint64_t keep = bad ? 0ull : ~0ull;
+  uint64_t* o = b.out + m * b.words;
+  o[0] = (s.v0[0] + s.v1[0] + s.mul0[0] + s.mul1[0]) & keep;
+  if (b.words >= 2) o[1] = (s.v0[1] + s.v1[1] + s.mul0[1] + s.mul1[1]) & keep;
+  if (b.words == 4) {
+    o[2] = (s.v0[2] + s.v1[2] + s.mul0[2] + s.mul1[2]) & keep;
+    o[3] = (s.v0[3] + s.v1[3] + s.mul0[3] + s.mul1[3]) & keep;
+  }
+}
+
 // Thread per message for batches whose messages are all at most kShortMax
 // bytes, in index order (neighbouring threads read neighbouring bytes).
 // Three blocks of 256 threads per SM (80 registers).
@@ -802,59 +840,95 @@ __global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, co
     for (int i = 0; i < 4; ++i) key[i] = __ldg(b.keys + i);
   }
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  // Offsets form: each thread's next two offsets are copied into shared
-  // memory one iteration ahead, so that the only global loads a message
-  // waits for are its own words.
-  __shared__ int64_t next_offsets[2][256][2];
-  const bool ahead = !kStream && b.offsets != nullptr && b.key_index == nullptr;
-  int cur = 0;
   const int64_t first_m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  auto fetch_offsets = [&](int64_t mm, int slot) {
-    cp_async8(smem_u32(&next_offsets[slot][threadIdx.x][0]), b.offsets + mm);
-    cp_async8(smem_u32(&next_offsets[slot][threadIdx.x][1]), b.offsets + mm + 1);
-    cp_async_commit();
-  };
-  if (ahead && first_m < b.n) fetch_offsets(first_m, 0);
-  for (int64_t m = first_m; m < b.n; m += stride) {
-    int64_t s0, len;
-    int bad;
-    if (ahead) {
-      cp_async_wait<0>();
-      const int64_t s = next_offsets[cur][threadIdx.x][0], e = next_offsets[cur][threadIdx.x][1];
-      if (m + stride < b.n) fetch_offsets(m + stride, cur ^ 1);
-      cur ^= 1;
-      bad = e < s ? kErrBadOffsets : 0;
-      s0 = s;
-      len = bad ? 0 : e - s;
-    } else {
+  if (kStream || b.offsets == nullptr || b.key_index != nullptr) {
+    for (int64_t m = first_m; m < b.n; m += stride) {
+      int64_t s0, len;
+      int bad;
       message_bounds(b, m, s0, len, bad);
-    }
-    if (bad) record_error(b.err, bad);
-    len = len < kShortMax ? len : kShortMax;
-    State s;
-    if constexpr (kStream) {
+      if (bad) record_error(b.err, bad);
+      len = len < kShortMax ? len : kShortMax;
+      State s;
       start_state(b, m, true, s);
       hash_short(s, base + s0, static_cast<uint32_t>(len), base + lo, base + hi);
       end_state(b, m, true, bad, s);
-      continue;
     }
-    if (!shared_key) {
+    return;
+  }
+  // Offsets form, pipelined one message ahead through shared memory: at the
+  // start of a message the thread copies the next message's two offsets, so
+  // that no message waits for its offsets.  With one key for the batch the
+  // thread also copies the next message's 17 words after this message's
+  // data packets; they land during the four finalisation rounds, and a
+  // message then waits for no global load at all.  (With a key per message
+  // the words are loaded directly: there the key load is waited for anyway,
+  // and staging the words measured slower.)  A word slot is 17 words (an odd
+  // stride: a warp's reads of one word hit 32 different banks).
+  __shared__ int64_t next_offsets[2][256][2];
+  __shared__ uint32_t next_words[2][256 * 17];
+  const int tid = threadIdx.x;
+  auto fetch_offsets = [&](int64_t mm, int slot) {
+    cp_async8(smem_u32(&next_offsets[slot][tid][0]), b.offsets + mm);
+    cp_async8(smem_u32(&next_offsets[slot][tid][1]), b.offsets + mm + 1);
+    cp_async_commit();
+  };
+  if (!shared_key) {
+    if (first_m < b.n) fetch_offsets(first_m, 0);
+    int cur = 0;
+    for (int64_t m = first_m; m < b.n; m += stride) {
+      cp_async_wait<0>();
+      const int64_t s0 = next_offsets[cur][tid][0], e0 = next_offsets[cur][tid][1];
+      if (m + stride < b.n) fetch_offsets(m + stride, cur ^ 1);
+      cur ^= 1;
+      const int bad = e0 < s0 ? kErrBadOffsets : 0;
+      int64_t len = bad ? 0 : e0 - s0;
+      len = len < kShortMax ? len : kShortMax;
+      if (bad) record_error(b.err, bad);
       const uint64_t* kp = key_of(b, m);
 #pragma unroll
       for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
+      State s;
+      init(s, key);
+      hash_short(s, base + s0, static_cast<uint32_t>(len), base + lo, base + hi);
+      finalize(s);
+      store_short_hash(b, m, bad, s);
     }
+    return;
+  }
+  auto fetch_words = [&](int slot) {  // the slot's offsets have landed
+    const int64_t s = next_offsets[slot][tid][0], e = next_offsets[slot][tid][1];
+    int64_t l = e < s ? 0 : e - s;
+    l = l < kShortMax ? l : kShortMax;
+    uint32_t* dst = &next_words[slot][17 * tid];
+    stage_short_words(dst, smem_u32(dst), base + s, static_cast<uint32_t>(l), base + lo, base + hi);
+  };
+  if (first_m >= b.n) return;
+  fetch_offsets(first_m, 0);
+  cp_async_wait<0>();
+  fetch_words(0);
+  int cur = 0;
+  for (int64_t m = first_m; m < b.n; m += stride) {
+    cp_async_wait<0>();  // this message's offsets and words are in slot cur
+    const int64_t s0 = next_offsets[cur][tid][0], e0 = next_offsets[cur][tid][1];
+    const int bad = e0 < s0 ? kErrBadOffsets : 0;
+    int64_t len = bad ? 0 : e0 - s0;
+    len = len < kShortMax ? len : kShortMax;
+    uint32_t x[17];
+#pragma unroll
+    for (int i = 0; i < 17; ++i) x[i] = next_words[cur][17 * tid + i];
+    const bool more = m + stride < b.n;
+    if (more) fetch_offsets(m + stride, cur ^ 1);
+    if (bad) record_error(b.err, bad);
+    State s;
     init(s, key);
-    hash_short(s, base + s0, static_cast<uint32_t>(len), base + lo, base + hi);
-    finalize(s);
-    // Only the lanes that are stored are summed (for 64-bit output, one).
-    const uint64_t keep = bad ? 0ull : ~0ull;
-    uint64_t* o = b.out + m * b.words;
-    o[0] = (s.v0[0] + s.v1[0] + s.mul0[0] + s.mul1[0]) & keep;
-    if (b.words >= 2) o[1] = (s.v0[1] + s.v1[1] + s.mul0[1] + s.mul1[1]) & keep;
-    if (b.words == 4) {
-      o[2] = (s.v0[2] + s.v1[2] + s.mul0[2] + s.mul1[2]) & keep;
-      o[3] = (s.v0[3] + s.v1[3] + s.mul0[3] + s.mul1[3]) & keep;
+    hash_short_words(s, x, static_cast<uint32_t>((base + s0) & 3), static_cast<uint32_t>(len));
+    if (more) {
+      cp_async_wait<0>();
+      fetch_words(cur ^ 1);
     }
+    cur ^= 1;
+    finalize(s);
+    store_short_hash(b, m, bad, s);
   }
 }
 
