@@ -316,8 +316,6 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
 
     K = args.steps
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     sampler = ClockSampler(local_rank)
     if dist:
         dist.barrier()
@@ -326,17 +324,19 @@ def run_ours(args, rank, world, local_rank):
     region0 = torch.cuda.Event(enable_timing=True)
     region1 = torch.cuda.Event(enable_timing=True)
     region0.record(stream)
-    for i in range(K):
-        starts[i].record(stream)
+    for _ in range(K):
         step()
-        ends[i].record(stream)
     region1.record(stream)
     torch.cuda.synchronize()
     sampler.stop()
     if dist:
         dist.barrier()
     region_ms = region0.elapsed_time(region1)
-    launch_ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
+    # Each step is one launch, back to back on one stream, so the kernel's
+    # average launch duration is the region over the launches: an upper
+    # bound that includes the gaps between launches.  (An event pair around
+    # every launch would itself add about 4 us per step.)
+    launch_ms = region_ms / (K * max(1, launches_per_step))
     if dist:
         t = torch.tensor([region_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
