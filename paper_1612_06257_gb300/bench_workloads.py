@@ -87,8 +87,28 @@ def small(ctx, dev):
     hot = e0.elapsed_time(e1) / 200
     cold, _ = _time(fn, 50, flush=lambda: junk.fill_(1))
     naive_cold = _naive_ms(ctx, fn, 50, flush=lambda: junk.fill_(1))
+    # The same launch replayed 20 times from a CUDA graph: the device-side
+    # latency without the host's per-call cost (the Python call alone takes
+    # a few microseconds).
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        fg = lambda: hh.hh_hash_fixed(ctx, 64, w.keys, 0, w.data, 1024, w.n, out=out,  # noqa: E731
+                                      stream=side)
+        fg()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=side):
+            for _ in range(20):
+                fg()
+    torch.cuda.current_stream().wait_stream(side)
+    graph.replay()
+    torch.cuda.synchronize()
+    g_ms, _ = _time(graph.replay, 10)
+    graph_us = g_ms / 20 * 1e3
     return {"workload": "4096 x 1024 B, one key, 64-bit (fixed-length batch)",
             "us_per_batch_hot_l2": round(hot * 1e3, 2), "us_per_batch_cold_l2": round(cold * 1e3, 2),
+            "us_per_batch_graph_replay": round(graph_us, 2),
             "naive_us_per_batch_cold_l2": round(naive_cold * 1e3, 2),
             "speedup_vs_naive_cold": round(naive_cold / cold, 2),
             "gbps_hot": round(w.total_bytes / hot / 1e6, 1),
