@@ -172,6 +172,46 @@ def test_short_messages_at_unaligned_batch_ends(ctx, kernel):
         assert np.array_equal(run_ragged(ctx, shifted, bits, kernel), oracle_hashes(w, bits))
 
 
+@pytest.mark.parametrize("per_message_keys", [False, True])
+def test_short_kernel_at_unaligned_batch_ends(ctx, per_message_keys):
+    """All messages of 0..64 bytes in a batch above the short kernel's minimum
+    size (10000 messages), with the byte buffer starting 3 bytes into an
+    allocation of other bytes and ending mid-word: the word windows of the
+    first and last messages cross the batch ends.  One key (the loop that
+    stages offsets and words in shared memory) or a key per message (the loop
+    that stages offsets only)."""
+    g = torch.Generator().manual_seed(41)
+    lengths = torch.randint(0, 65, (10000,), generator=g)
+    lengths[0], lengths[1], lengths[-2], lengths[-1] = 63, 2, 1, 61
+    w = workloads.from_lengths(lengths, seed=41, device=DEV, per_message_keys=per_message_keys)
+    backing = torch.randint(0, 256, (w.total_bytes + 8,), dtype=torch.uint8, device=DEV)
+    backing[3:3 + w.total_bytes] = w.data
+    view = backing[3:3 + w.total_bytes]
+    shifted = workloads.Workload("short", view, w.offsets, None, w.keys, per_message_keys, w.n)
+    for bits in (64, 128):
+        assert np.array_equal(run_ragged(ctx, shifted, bits), oracle_hashes(w, bits))
+
+
+@pytest.mark.parametrize("per_message_keys", [False, True])
+def test_short_kernel_flags_decreasing_offsets(ctx, per_message_keys):
+    """A descriptor with end < start inside an all-short batch of 10000
+    messages: the short kernel records the error and writes a zero hash for
+    that message; every other message is hashed as its offsets say."""
+    g = torch.Generator().manual_seed(43)
+    lengths = torch.randint(0, 65, (10000,), generator=g)
+    lengths[5000], lengths[5001] = 20, 10
+    w = workloads.from_lengths(lengths, seed=43, device=DEV, per_message_keys=per_message_keys)
+    bad = w.offsets.clone()
+    bad[5001] = bad[5000] - 3  # message 5000 ends before it starts; 5001 grows to 33 bytes
+    broken = workloads.Workload("short", w.data, bad, None, w.keys, per_message_keys, w.n)
+    out = hh.hh_hash128_batch(ctx, w.keys, w.key_mode, w.data, bad)
+    assert hh.hh_get_device_error(ctx) == hh.HH_ERR_BAD_OFFSETS
+    got = as_u64(out, 2)
+    assert got[5000].tolist() == [0, 0]
+    others = np.array([i for i in range(w.n) if i != 5000])
+    assert np.array_equal(got[others], oracle_hashes(broken, 128, indices=others))
+
+
 def test_output_guard_words_untouched(ctx):
     w = workloads.ragged(3000, seed=11, device=DEV, max_len=3000)
     out = torch.full((3000 * 2 + 64,), -0x5A5A5A5A5A5A5A5B, dtype=torch.int64, device=DEV)
@@ -295,7 +335,7 @@ def _segments_case(n, seed, max_len, pool_bytes, key_rows):
 
 
 @pytest.mark.parametrize("kernel", ["auto", "unsorted", "naive"])
-@pytest.mark.parametrize("n,max_len", [(700, 3000), (5000, 64), (4000, 70000)])
+@pytest.mark.parametrize("n,max_len", [(700, 3000), (5000, 64), (12000, 64), (4000, 70000)])
 def test_segments_with_key_table(ctx, kernel, n, max_len):
     """Segments of one pool in random order (overlapping), keys from a device
     key table by index: the request-server batch form."""
