@@ -24,7 +24,7 @@ constexpr int64_t kSortMinMessages = 1;
 constexpr int64_t kMaxSortedMessages = 0x7FFFFFFFll;
 constexpr int64_t kShortKernelMinMessages = 8192;  // smaller batches: warp-tile kernel only
 constexpr int64_t kFixedRows = 128;                // messages per TMA tile at one per thread
-constexpr size_t kHostChunkBytes = size_t(64) << 20;  // payload per host-path chunk
+constexpr size_t kHostChunkBytes = size_t(128) << 20;  // payload per host-path chunk
 constexpr int64_t kHostChunkMessages = int64_t(1) << 20;
 
 using hh::DeviceGuard;
