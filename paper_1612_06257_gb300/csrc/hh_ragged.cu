@@ -6,8 +6,9 @@
 // Warps never wait on one another: no CTA barrier, a warp-private ring, and
 // warp tiles taken from a queue (longest first after the length sort).
 //
-// Loading a stage: row r's window is the 16-byte aligned span around bytes
-// [kW, kW + W) of message r.  Four lanes copy each row, so one cp.async.cg
+// Loading a stage: a message's window is the 16-byte aligned span around
+// bytes [kW, kW + W) of it, in the row its lane owns.  Four lanes copy each
+// row, so one cp.async.cg
 // instruction moves 64 contiguous bytes of 8 rows (8 cache lines for 512
 // bytes); a row's base address and chunk range come from its owner lane by
 // shuffle, and chunk offsets fold into the instruction's immediate.  Only
@@ -18,8 +19,14 @@
 // all their chunks with no per-chunk tests.
 //
 // Reading a packet: when every message of the warp tile starts 16-byte
-// aligned, two 128-bit shared loads; otherwise nine 32-bit loads from the
-// enclosing words and one PRMT per word to shift the bytes into place.
+// aligned, two 128-bit shared loads; otherwise the nine enclosing 32-bit
+// words (eight new ones per packet: consecutive packets share one) and one
+// PRMT per word to shift the bytes into place.  Rows are assigned so that
+// lanes whose messages start at the same word of a 16-byte block spread over
+// the shared-memory banks.
+//
+// Batches of messages of at most 64 bytes run in short_kernel instead (one
+// thread per message, pipelined through shared memory).
 #include <cuda_runtime.h>
 
 #include <cstdint>
