@@ -38,6 +38,36 @@ __device__ __forceinline__ int bucket_of(const Batch& b, int64_t i) {
   return bucket_of_packets((len + 31) >> 5);
 }
 
+// Buckets of this thread's kPerThread elements of chunk c (-1 past n).  In
+// the plain offsets form every offset is loaded first, unconditionally (at
+// a clamped index), so that all the loads are in flight together; the
+// general form goes through message_length one element at a time.
+__device__ __forceinline__ void bucket_keys(const Batch& b, int64_t n, int64_t c,
+                                            int key[kPerThread]) {
+  if (b.offsets != nullptr && b.key_index == nullptr && b.stream_mode != kStreamUpdate) {
+    int64_t s[kPerThread], e[kPerThread];
+#pragma unroll
+    for (int k = 0; k < kPerThread; ++k) {
+      const int64_t i = c + k * kSortThreads + threadIdx.x;
+      const int64_t j = i < n ? i : n - 1;
+      s[k] = b.offsets[j];
+      e[k] = b.offsets[j + 1];
+    }
+#pragma unroll
+    for (int k = 0; k < kPerThread; ++k) {
+      const int64_t i = c + k * kSortThreads + threadIdx.x;
+      const int64_t len = e[k] - s[k];  // negative: a bad descriptor, hashed as empty
+      key[k] = i >= n ? -1 : len <= 0 ? 0 : bucket_of_packets((len + 31) >> 5);
+    }
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < kPerThread; ++k) {
+    const int64_t i = c + k * kSortThreads + threadIdx.x;
+    key[k] = i < n ? bucket_of(b, i) : -1;
+  }
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -53,10 +83,11 @@ __global__ void __launch_bounds__(kSortThreads) bucket_count_kernel(Batch b, uin
   const int lane = threadIdx.x & 31;
   for (int64_t c = static_cast<int64_t>(blockIdx.x) * kChunk; c < n;
        c += static_cast<int64_t>(gridDim.x) * kChunk) {
+    int keys[kPerThread];
+    bucket_keys(b, n, c, keys);
 #pragma unroll
     for (int e = 0; e < kPerThread; ++e) {
-      const int64_t i = c + e * kSortThreads + threadIdx.x;
-      const int key = i < n ? bucket_of(b, i) : -1;
+      const int key = keys[e];
       const unsigned peers = __match_any_sync(0xffffffffu, key);
       if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[key], __popc(peers));
     }
@@ -149,10 +180,9 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_
 __device__ __forceinline__ void rank_chunk(const Batch& b, int64_t n, int64_t c, uint32_t* cnt,
                                            int key[kPerThread], uint32_t rank[kPerThread]) {
   const int lane = threadIdx.x & 31;
+  bucket_keys(b, n, c, key);
 #pragma unroll
   for (int e = 0; e < kPerThread; ++e) {
-    const int64_t i = c + e * kSortThreads + threadIdx.x;
-    key[e] = i < n ? bucket_of(b, i) : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, key[e]);
     const int leader = __ffs(peers) - 1;
     uint32_t first = 0;
