@@ -44,7 +44,7 @@ __device__ __forceinline__ int bucket_of(const Batch& b, int64_t i) {
 // general form goes through message_length one element at a time.
 __device__ __forceinline__ void bucket_keys(const Batch& b, int64_t n, int64_t c,
                                             int key[kPerThread]) {
-  if (b.offsets != nullptr && b.key_index == nullptr && b.stream_mode != kStreamUpdate) {
+  if (n > 0 && b.offsets != nullptr && b.key_index == nullptr && b.stream_mode != kStreamUpdate) {
     int64_t s[kPerThread], e[kPerThread];
 #pragma unroll
     for (int k = 0; k < kPerThread; ++k) {
