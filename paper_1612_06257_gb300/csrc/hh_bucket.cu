@@ -74,6 +74,11 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
+// Buckets 0 .. kRegBuckets - 1 (messages of at most 96 bytes) are counted
+// in registers and reduced once per warp: batches of short messages would
+// otherwise send every element through the warp-aggregated atomics.
+constexpr int kRegBuckets = 4;
+
 __global__ void __launch_bounds__(kSortThreads) bucket_count_kernel(Batch b, uint32_t* hist) {
   resolve_count(b);
   const int64_t n = b.n;
@@ -81,6 +86,7 @@ __global__ void __launch_bounds__(kSortThreads) bucket_count_kernel(Batch b, uin
   for (int i = threadIdx.x; i < kBuckets; i += kSortThreads) h[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  uint32_t small[kRegBuckets] = {};
   for (int64_t c = static_cast<int64_t>(blockIdx.x) * kChunk; c < n;
        c += static_cast<int64_t>(gridDim.x) * kChunk) {
     int keys[kPerThread];
@@ -88,9 +94,21 @@ __global__ void __launch_bounds__(kSortThreads) bucket_count_kernel(Batch b, uin
 #pragma unroll
     for (int e = 0; e < kPerThread; ++e) {
       const int key = keys[e];
-      const unsigned peers = __match_any_sync(0xffffffffu, key);
-      if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[key], __popc(peers));
+#pragma unroll
+      for (int q = 0; q < kRegBuckets; ++q) small[q] += key == q ? 1u : 0u;
+      const int big = key >= kRegBuckets ? key : -1;
+      if (__any_sync(0xffffffffu, big >= 0)) {
+        const unsigned peers = __match_any_sync(0xffffffffu, big);
+        if (big >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[big], __popc(peers));
+      }
     }
+  }
+#pragma unroll
+  for (int q = 0; q < kRegBuckets; ++q) {
+    uint32_t v = small[q];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if (lane == 0 && v) atomicAdd(&h[q], v);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kBuckets; i += kSortThreads)
