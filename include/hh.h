@@ -82,13 +82,15 @@ enum hh_kernel {
 
 /*
  * Create a context on CUDA device `device`.  It owns a small device error
- * word, a work-queue counter and scratch memory for the length sort, which
- * grows when a call needs more (see hh_reserve).  `tune_cache_path` names a
- * tuning table written by hh_tune_save (HH_ERR_INVALID_ARG if it cannot be
- * read), or NULL for the built-in choices measured on GB300.
+ * word, the work-queue counters and the length sort's scratch memory, sized
+ * for HH_DEFAULT_MAX_MESSAGES messages per call (16 MiB; raise it with
+ * hh_reserve).  `tune_cache_path` names a tuning table written by
+ * hh_tune_save (HH_ERR_INVALID_ARG if it cannot be read), or NULL for the
+ * built-in choices measured on GB300.
  * Returns HH_ERR_NO_DEVICE when the device is absent or not sm_103a.
  * The caller's current device is restored before returning.
  */
+#define HH_DEFAULT_MAX_MESSAGES (1 << 22)
 int hh_init(hh_ctx** out, int device, const char* tune_cache_path);
 
 /* Free everything the context owns.  Waits for its device work first.
@@ -96,11 +98,14 @@ int hh_init(hh_ctx** out, int device, const char* tune_cache_path);
 int hh_destroy(hh_ctx* ctx);
 
 /*
- * Pre-allocate scratch for batches of up to `max_messages` messages, so that
- * later calls of that size allocate nothing (and can be captured into a CUDA
- * graph).  A hash call with more messages grows the scratch itself, which
- * synchronises the device; inside a stream capture it returns
- * HH_ERR_TOO_LARGE instead.
+ * Size the context's length-sort scratch for batches of up to `max_messages`
+ * messages (4 bytes per message; it never shrinks).  The hash calls
+ * themselves never allocate or synchronise: a ragged, segments or stream
+ * call with more messages than the context has room for returns
+ * HH_ERR_TOO_LARGE and enqueues nothing (fixed-length batches need no
+ * scratch).  Growing the scratch synchronises the device, so reserve before
+ * a latency-critical phase or a stream capture.  HH_ERR_TOO_LARGE above
+ * 2^31 - 1 messages.
  */
 int hh_reserve(hh_ctx* ctx, int64_t max_messages);
 
@@ -166,10 +171,16 @@ int hh_hash_segments(hh_ctx* ctx, int bits, const uint64_t* key_table, int32_t k
 /*
  * Host-memory variant of the ragged call: keys, bytes, offsets and out are
  * HOST pointers (pinned memory gives full copy speed; pageable works).  The
- * batch is copied to the device in chunks, hashed there and copied back,
- * with copies and hashing of consecutive chunks overlapped.  Synchronous:
- * returns after `out` is filled.  Device staging memory is owned by the
- * context and grows on first use.  bits is 64, 128 or 256.
+ * batch is copied to the device in chunks of at most 128 MiB and 2^20
+ * messages, hashed there and copied back, with copies and hashing of
+ * consecutive chunks overlapped.  Synchronous: returns after `out` is
+ * filled, or, on an error, after every copy it started has finished.  Before
+ * a chunk is enqueued its offsets are checked on the host: a decreasing pair
+ * returns HH_ERR_BAD_OFFSETS (the hashes of earlier chunks are written, the
+ * rest of `out` is not).  Unlike the device calls it owns device staging
+ * memory (two chunk slots), which it grows on the first call that needs
+ * more; the growth is stream-ordered on the context's own copy stream and
+ * waits for no other work on the device.  bits is 64, 128 or 256.
  */
 int hh_hash_host(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
                  const uint8_t* bytes, const int64_t* offsets, int64_t n, uint64_t* out);

@@ -150,6 +150,7 @@ def _update_ceiling(ctx, dev):
 
 def short(ctx, dev):
     w = workloads.short(1 << 26, seed=3, device=dev)
+    hh.hh_reserve(ctx, w.n)  # beyond the default sort scratch of 2^22 messages
     lengths = (w.offsets[1:] - w.offsets[:-1]).cpu().numpy()
     upd_per_hash = float(np.mean(lengths // 32 + (lengths % 32 != 0) + 4))
     ceiling = _update_ceiling(ctx, dev) / upd_per_hash

@@ -35,17 +35,16 @@ int to_status(cudaError_t e) {
   return HH_ERR_CUDA;
 }
 
-bool stream_capturing(cudaStream_t s) {
-  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
-  return st != cudaStreamCaptureStatusNone;
-}
-
-int ensure_perm(hh_ctx* ctx, int64_t n, cudaStream_t stream) {
+// Grow the length sort's message-order scratch to `n` entries.  Only
+// hh_init and hh_reserve call this: the hash calls themselves never allocate
+// (a batch beyond the reserved size returns HH_ERR_TOO_LARGE instead).
+int reserve_perm(hh_ctx* ctx, int64_t n) {
   if (n <= ctx->perm_cap) return HH_OK;
-  if (stream_capturing(stream)) return HH_ERR_TOO_LARGE;
-  if (cudaDeviceSynchronize() != cudaSuccess) return HH_ERR_CUDA;
-  if (ctx->d_perm) cudaFree(ctx->d_perm);
+  if (ctx->d_perm) {
+    // The old array may still be read by work queued on any stream.
+    if (cudaDeviceSynchronize() != cudaSuccess) return HH_ERR_CUDA;
+    cudaFree(ctx->d_perm);
+  }
   ctx->d_perm = nullptr;
   ctx->perm_cap = 0;
   if (cudaMalloc(&ctx->d_perm, sizeof(int32_t) * static_cast<size_t>(n)) != cudaSuccess)
@@ -91,9 +90,8 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
   const bool sort = !fixed && ctx->kernel != HH_KERNEL_STAGED_UNSORTED && n >= kSortMinMessages;
   hh::Queue q{};
   if (sort) {
-    if (n > kMaxSortedMessages) return HH_ERR_TOO_LARGE;
-    int st = ensure_perm(ctx, n, stream);
-    if (st != HH_OK) return st;
+    // The batch must fit the scratch reserved by hh_init / hh_reserve.
+    if (n > ctx->perm_cap) return HH_ERR_TOO_LARGE;
     int launches = 0;
     cudaError_t e = hh::launch_bucket_sort(b, ctx->d_hist, ctx->d_cursor, ctx->d_perm,
                                            ctx->d_next_tile, ctx->d_use_perm, ctx->d_huge,
@@ -165,14 +163,19 @@ int hash_common(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode, const
   return hash_device(ctx, b, stream);
 }
 
+// Grow one device buffer of the host-buffer path, stream-ordered on the
+// context's copy stream: the old buffer is released after everything queued
+// there (which includes the slot's last use), and nothing outside the
+// context's own streams waits.
 template <typename T>
-int grow(T** p, size_t* cap, size_t need) {
+int grow(T** p, size_t* cap, size_t need, cudaStream_t s) {
   if (need <= *cap) return HH_OK;
   const size_t want = std::max(need, *cap + *cap / 2);
-  if (*p) cudaFree(*p);
+  if (*p) cudaFreeAsync(*p, s);
   *p = nullptr;
   *cap = 0;
-  if (cudaMalloc(reinterpret_cast<void**>(p), want * sizeof(T)) != cudaSuccess) return HH_ERR_NO_MEMORY;
+  if (cudaMallocAsync(reinterpret_cast<void**>(p), want * sizeof(T), s) != cudaSuccess)
+    return HH_ERR_NO_MEMORY;
   *cap = want;
   return HH_OK;
 }
@@ -258,7 +261,8 @@ int hh_init(hh_ctx** out, int device, const char* tune_cache_path) {
             cudaMalloc(&ctx->d_hist, sizeof(uint32_t) * hh::kBuckets) == cudaSuccess &&
             cudaMalloc(&ctx->d_cursor, sizeof(uint32_t) * hh::kBuckets) == cudaSuccess &&
             cudaMemset(ctx->d_err, 0, sizeof(int)) == cudaSuccess &&
-            cudaMemset(ctx->d_next_tile, 0, 4 * sizeof(unsigned long long)) == cudaSuccess;
+            cudaMemset(ctx->d_next_tile, 0, 4 * sizeof(unsigned long long)) == cudaSuccess &&
+            reserve_perm(ctx, HH_DEFAULT_MAX_MESSAGES) == HH_OK;
   if (!ok) {
     hh_destroy(ctx);
     return HH_ERR_NO_MEMORY;
@@ -279,15 +283,21 @@ int hh_destroy(hh_ctx* ctx) {
   cudaFree(ctx->d_cursor);
   cudaFree(ctx->d_perm);
   for (hh::HostSlot& s : ctx->slots) {
-    cudaFree(s.bytes);
-    cudaFree(s.offsets);
-    cudaFree(s.keys);
-    cudaFree(s.out);
+    // Allocated stream-ordered on s_h2d (see grow); freed the same way.
+    if (ctx->s_h2d) {
+      if (s.bytes) cudaFreeAsync(s.bytes, ctx->s_h2d);
+      if (s.offsets) cudaFreeAsync(s.offsets, ctx->s_h2d);
+      if (s.keys) cudaFreeAsync(s.keys, ctx->s_h2d);
+      if (s.out) cudaFreeAsync(s.out, ctx->s_h2d);
+    }
     if (s.staged) cudaEventDestroy(s.staged);
     if (s.hashed) cudaEventDestroy(s.hashed);
     if (s.drained) cudaEventDestroy(s.drained);
   }
-  if (ctx->s_h2d) cudaStreamDestroy(ctx->s_h2d);
+  if (ctx->s_h2d) {
+    cudaStreamSynchronize(ctx->s_h2d);
+    cudaStreamDestroy(ctx->s_h2d);
+  }
   if (ctx->s_comp) cudaStreamDestroy(ctx->s_comp);
   if (ctx->s_d2h) cudaStreamDestroy(ctx->s_d2h);
   delete ctx;
@@ -299,7 +309,7 @@ int hh_reserve(hh_ctx* ctx, int64_t max_messages) {
   if (max_messages > kMaxSortedMessages) return HH_ERR_TOO_LARGE;
   DeviceGuard guard(ctx->device);
   if (!guard.ok) return HH_ERR_CUDA;
-  return ensure_perm(ctx, max_messages, nullptr);
+  return reserve_perm(ctx, max_messages);
 }
 
 int hh_hash64_batch(hh_ctx* ctx, const uint64_t* keys, int key_mode, const uint8_t* bytes,
@@ -430,6 +440,18 @@ int hh_hash_host(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
         return HH_ERR_CUDA;
     }
   }
+  // Once a chunk is enqueued, an error return first waits for the context's
+  // streams, so that no copy still reads `bytes` or writes `out` after the
+  // call has returned.
+  bool enqueued = false;
+  auto fail = [&](int status) {
+    if (enqueued) {
+      cudaStreamSynchronize(ctx->s_h2d);
+      cudaStreamSynchronize(ctx->s_comp);
+      cudaStreamSynchronize(ctx->s_d2h);
+    }
+    return status;
+  };
   // Chunk boundaries: at most kHostChunkMessages messages and (unless a single
   // message is larger) kHostChunkBytes payload per chunk.
   int launches = 0;
@@ -448,27 +470,33 @@ int hh_hash_host(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
       }
       m1 = lo;
     }
-    if (offsets[m1] < offsets[m0]) return HH_ERR_BAD_OFFSETS;
+    // Only the chunk's own bytes are staged, so every offset inside it must
+    // lie between its end offsets: check that none decreases before any of
+    // the chunk is enqueued.  (offsets[m0] >= offsets[0] >= 0 follows from
+    // the checks of the earlier chunks.)
+    {
+      bool decreasing = false;
+      for (int64_t i = m0; i < m1; ++i) decreasing |= offsets[i + 1] < offsets[i];
+      if (decreasing) return fail(HH_ERR_BAD_OFFSETS);
+    }
     hh::HostSlot& s = ctx->slots[chunk_index & 1];
     const int64_t cn = m1 - m0;
     const size_t cbytes = static_cast<size_t>(offsets[m1] - offsets[m0]);
     // The slot's previous chunk must have drained before its buffers change.
-    if (cudaStreamWaitEvent(ctx->s_h2d, s.drained, 0) != cudaSuccess) return HH_ERR_CUDA;
-    if (cbytes > s.bytes_cap || static_cast<size_t>(cn + 1) > s.offsets_cap ||
-        static_cast<size_t>(cn) * words > s.out_cap ||
-        (key_mode == HH_KEY_PER_MESSAGE && static_cast<size_t>(cn) * 4 > s.keys_cap) ||
-        s.keys_cap < 4) {
-      if (cudaDeviceSynchronize() != cudaSuccess) return HH_ERR_CUDA;
-      int st = grow(&s.bytes, &s.bytes_cap, std::max<size_t>(cbytes, 16));
-      if (st == HH_OK) st = grow(&s.offsets, &s.offsets_cap, static_cast<size_t>(cn + 1));
-      if (st == HH_OK) st = grow(&s.out, &s.out_cap, static_cast<size_t>(cn) * words);
+    if (cudaStreamWaitEvent(ctx->s_h2d, s.drained, 0) != cudaSuccess) return fail(HH_ERR_CUDA);
+    {
+      int st = grow(&s.bytes, &s.bytes_cap, std::max<size_t>(cbytes, 16), ctx->s_h2d);
+      if (st == HH_OK) st = grow(&s.offsets, &s.offsets_cap, static_cast<size_t>(cn + 1), ctx->s_h2d);
+      if (st == HH_OK) st = grow(&s.out, &s.out_cap, static_cast<size_t>(cn) * words, ctx->s_h2d);
       if (st == HH_OK)
         st = grow(&s.keys, &s.keys_cap,
-                  key_mode == HH_KEY_PER_MESSAGE ? static_cast<size_t>(cn) * 4 : size_t(4));
-      if (st != HH_OK) return st;
+                  key_mode == HH_KEY_PER_MESSAGE ? static_cast<size_t>(cn) * 4 : size_t(4),
+                  ctx->s_h2d);
+      if (st != HH_OK) return fail(st);
     }
     const uint64_t* ck = key_mode == HH_KEY_PER_MESSAGE ? keys + 4 * m0 : keys;
     const size_t key_words = key_mode == HH_KEY_PER_MESSAGE ? static_cast<size_t>(cn) * 4 : 4;
+    enqueued = true;
     cudaError_t e = cudaMemcpyAsync(s.bytes, bytes + offsets[m0], cbytes, cudaMemcpyHostToDevice,
                                     ctx->s_h2d);
     if (e == cudaSuccess)
@@ -479,29 +507,29 @@ int hh_hash_host(hh_ctx* ctx, int bits, const uint64_t* keys, int key_mode,
                           ctx->s_h2d);
     if (e == cudaSuccess) e = cudaEventRecord(s.staged, ctx->s_h2d);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_comp, s.staged, 0);
-    if (e != cudaSuccess) return HH_ERR_CUDA;
+    if (e != cudaSuccess) return fail(HH_ERR_CUDA);
     // The device offsets are absolute; shift the base so that
     // base + offsets[m0] is the first staged byte.
     const uint8_t* dev_base = s.bytes - offsets[m0];
     int st = hash_common(ctx, bits, s.keys, key_mode, dev_base, s.offsets, 0, cn, s.out,
                          ctx->s_comp);
     launches += ctx->last_launches;
-    if (st != HH_OK) return st;
+    if (st != HH_OK) return fail(st);
     e = cudaEventRecord(s.hashed, ctx->s_comp);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_d2h, s.hashed, 0);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(out + m0 * words, s.out, sizeof(uint64_t) * cn * words,
                           cudaMemcpyDeviceToHost, ctx->s_d2h);
     if (e == cudaSuccess) e = cudaEventRecord(s.drained, ctx->s_d2h);
-    if (e != cudaSuccess) return HH_ERR_CUDA;
+    if (e != cudaSuccess) return fail(HH_ERR_CUDA);
     m0 = m1;
     ++chunk_index;
   }
   ctx->last_launches = launches;
-  if (cudaStreamSynchronize(ctx->s_d2h) != cudaSuccess) return HH_ERR_CUDA;
+  if (cudaStreamSynchronize(ctx->s_d2h) != cudaSuccess) return fail(HH_ERR_CUDA);
   int err = 0;
   if (cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-    return HH_ERR_CUDA;
+    return fail(HH_ERR_CUDA);
   if (err != 0) {
     cudaMemset(ctx->d_err, 0, sizeof(int));
     return err;

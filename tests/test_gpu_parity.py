@@ -313,6 +313,7 @@ def test_full_size_ragged_4m_messages(ctx):
 def test_full_size_short_64m_messages(ctx, bits):
     """2^26 messages of 0..64 bytes, 10% all zero, one key."""
     w = workloads.short(1 << 26, seed=23, device=DEV)
+    hh.hh_reserve(ctx, w.n)  # beyond the default sort scratch of 2^22 messages
     got = run_ragged(ctx, w, bits)
     idx = _sample(w.n, 20000, 23)
     assert np.array_equal(got[idx], oracle_hashes(w, bits, indices=idx))
