@@ -290,6 +290,16 @@ int hh_autotune(hh_ctx* ctx, int64_t max_device_bytes);
  *                  one.
  * HH_ERR_INVALID_ARG for another name or a value out of range.  Results
  * never depend on these settings.
+ *
+ * One more name sets a property of the context, not of the tuning table
+ * (hh_tune_save does not write it):
+ *   "wait_limit_ns" >= 0: how long a kernel waits for one asynchronous copy
+ *                  before it gives up (default 2e9, 2 s; 0 tests the copy's
+ *                  barrier once without blocking).  A kernel that gives up
+ *                  records HH_ERR_TIMEOUT in the device error word, issues no
+ *                  further copies, waits for the copies it issued (at most
+ *                  0.2 s each) and writes zero hashes for the messages it
+ *                  did not finish; messages it finished are hashed exactly.
  */
 int hh_set_tune_param(hh_ctx* ctx, const char* name, int value);
 

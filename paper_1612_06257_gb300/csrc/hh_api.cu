@@ -63,6 +63,7 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
   DeviceGuard guard(ctx->device);
   if (!guard.ok) return HH_ERR_CUDA;
   b.err = ctx->d_err;
+  b.wait_ns = ctx->wait_limit_ns;
   const int64_t n = b.n;
   const bool fixed = b.offsets == nullptr && b.seg_start == nullptr;
 

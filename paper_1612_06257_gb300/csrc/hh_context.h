@@ -83,6 +83,7 @@ struct hh_ctx {
   hh::StagedShape shape_bulk{256, 2};  // per-thread bulk-copy kernel
   int last_launches = 0;
   bool tuning = false;  // hh_autotune is timing shapes: no small-batch override
+  uint64_t wait_limit_ns = hh::kWaitLimitNs;  // limit of one wait for an asynchronous copy
   // Host-buffer path.
   cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
   hh::HostSlot slots[2];

@@ -15,6 +15,21 @@
 // 8 distinct chunks (all 32 banks) on every 128-bit shared load.  Bytes past
 // the end of a message and rows past the end of the batch are zero-filled by
 // the TMA unit; they are never hashed.
+//
+// Giving up (a barrier wait that runs past the context's limit) is
+// CTA-wide.  The thread that gives up sets a shared flag before its warp
+// arrives on the "empty" barrier; every thread reads the flag before each
+// wait and from then on neither waits nor hashes, and writes zero hashes.
+// Thread 0 refills a buffer only after it has itself seen the buffer's
+// previous load land and, after the "empty" wait, found the flag clear; so
+// at most one load per buffer is ever in flight, no "full" phase is armed
+// twice, and no buffer is overwritten after the flag is set (a warp that
+// raced ahead after giving up can complete an "empty" phase early, but only
+// after setting the flag, which the refill check then sees).  Thread 0
+// counts the loads it issued and the prefix of them it saw land; before the
+// CTA exits it waits (kDrainLimitNs each) for every load of the difference,
+// load q on buffer q mod NST at phase parity (q / NST) mod 2, so no bulk copy
+// is still writing shared memory when the CTA's shared memory is released.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -39,7 +54,16 @@ struct FixedParams {
   int words;
   int* err;
   uint32_t one;
+  uint64_t wait_ns;  // limit of one barrier wait (0: a single non-blocking test)
 };
+
+// Give up on the pipeline: every thread of the CTA stops waiting and hashing
+// once it sees the flag, and the producer issues no further load.
+__device__ __forceinline__ void give_up(volatile int* flag, int* err) {
+  *flag = 1;
+  __threadfence_block();
+  record_error(err, kErrTimeout);
+}
 
 template <int W, int NST, int M>
 struct FixedLayout {
@@ -78,6 +102,8 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = my_tiles * steps;                    // this CTA's (tile, window) stream
 
+  __shared__ int s_abort;
+  volatile int* abort_flag = &s_abort;
   if (t == 0) {
     prefetch_tensormap(&tmap);
     for (int i = 0; i < NST; ++i) {
@@ -85,12 +111,14 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
       mbar_init(&empty[i], kRows / 32);
     }
     fence_mbar_init();
+    s_abort = 0;
   }
   __syncthreads();
 
   // Producer cursor (thread 0 only): the (tile, window) of the next load.
   int64_t p_tile = blockIdx.x, p_k = 0;
   int p_buf = 0;
+  int64_t issued = 0, confirmed = 0;  // loads issued / the prefix seen landed
   auto issue_next = [&]() {
     mbar_arrive_expect_tx(&full[p_buf], L::kStageBytes);
 #pragma unroll
@@ -105,6 +133,7 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
       p_tile += gridDim.x;
     }
     p_buf = (p_buf + 1 == NST) ? 0 : p_buf + 1;
+    ++issued;
   };
   if (t == 0)
     for (int64_t g = 0; g < NST && g < total; ++g) issue_next();
@@ -136,9 +165,13 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
       init(s[i], key);
     }
     for (int64_t k = 0; k < steps; ++k, ++g) {
-      if (ok && !mbar_wait_bounded(&full[b], parity, kWaitLimitNs)) {
-        ok = false;
-        record_error(p.err, kErrTimeout);
+      if (ok) {
+        if (*abort_flag != 0) {
+          ok = false;
+        } else if (!mbar_wait_bounded(&full[b], parity, p.wait_ns)) {
+          ok = false;
+          give_up(abort_flag, p.err);
+        }
       }
       const uint8_t* stage = smem + b * L::kStageBytes;
       if (ok) {
@@ -166,13 +199,17 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
-      if (t == 0 && g + NST < total) {
-        // Refill this buffer once every warp has read it.
-        if (!mbar_wait_bounded(&empty[b], parity, kWaitLimitNs)) {
-          record_error(p.err, kErrTimeout);
-        } else {
-          fence_proxy_async_smem();
-          issue_next();
+      if (t == 0 && ok) {
+        confirmed = g + 1;  // this thread saw load g land
+        if (g + NST < total) {
+          // Refill this buffer once every warp has read it, unless some
+          // thread has given up.
+          if (!mbar_wait_bounded(&empty[b], parity, p.wait_ns)) {
+            give_up(abort_flag, p.err);
+          } else if (*abort_flag == 0) {
+            fence_proxy_async_smem();
+            issue_next();
+          }
         }
       }
       if (++b == NST) {
@@ -199,11 +236,11 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
       }
     }
   }
-  // Loads issued but never waited for (only after a timeout) get a bounded
-  // time to land before the CTA exits.
-  if (!ok && t == 0) {
-    for (int i = 0; i < NST; ++i) mbar_wait_bounded(&full[i], 0, kDrainLimitNs);
-  }
+  // Loads issued but not seen landing (only after giving up) land before
+  // the CTA exits.
+  if (t == 0)
+    for (int64_t q = confirmed; q < issued; ++q)
+      mbar_wait_bounded(&full[q % NST], static_cast<uint32_t>((q / NST) & 1), kDrainLimitNs);
 }
 
 // Two threads per message, for batches too small to fill the GPU: threads
@@ -239,6 +276,8 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = my_tiles * steps;
 
+  __shared__ int s_abort;
+  volatile int* abort_flag = &s_abort;
   if (t == 0) {
     prefetch_tensormap(&tmap);
     for (int i = 0; i < NST; ++i) {
@@ -246,11 +285,13 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
       mbar_init(&empty[i], kWarps);
     }
     fence_mbar_init();
+    s_abort = 0;
   }
   __syncthreads();
 
   int64_t p_tile = blockIdx.x, p_k = 0;
   int p_buf = 0;
+  int64_t issued = 0, confirmed = 0;  // loads issued / the prefix seen landed
   auto issue_next = [&]() {
     mbar_arrive_expect_tx(&full[p_buf], L::kStageBytes);
 #pragma unroll
@@ -263,6 +304,7 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
       p_tile += gridDim.x;
     }
     p_buf = (p_buf + 1 == NST) ? 0 : p_buf + 1;
+    ++issued;
   };
   if (t == 0)
     for (int64_t g = 0; g < NST && g < total; ++g) issue_next();
@@ -290,9 +332,13 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
     }
     init_half(s, key, half);
     for (int64_t k = 0; k < steps; ++k, ++g) {
-      if (ok && !mbar_wait_bounded(&full[b], parity, kWaitLimitNs)) {
-        ok = false;
-        record_error(p.err, kErrTimeout);
+      if (ok) {
+        if (*abort_flag != 0) {
+          ok = false;
+        } else if (!mbar_wait_bounded(&full[b], parity, p.wait_ns)) {
+          ok = false;
+          give_up(abort_flag, p.err);
+        }
       }
       const uint8_t* stage = smem + b * L::kStageBytes;
       if (ok) {
@@ -316,12 +362,15 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
-      if (t == 0 && g + NST < total) {
-        if (!mbar_wait_bounded(&empty[b], parity, kWaitLimitNs)) {
-          record_error(p.err, kErrTimeout);
-        } else {
-          fence_proxy_async_smem();
-          issue_next();
+      if (t == 0 && ok) {
+        confirmed = g + 1;  // this thread saw load g land
+        if (g + NST < total) {
+          if (!mbar_wait_bounded(&empty[b], parity, p.wait_ns)) {
+            give_up(abort_flag, p.err);
+          } else if (*abort_flag == 0) {
+            fence_proxy_async_smem();
+            issue_next();
+          }
         }
       }
       if (++b == NST) {
@@ -344,9 +393,9 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
       }
     }
   }
-  if (!ok && t == 0) {
-    for (int i = 0; i < NST; ++i) mbar_wait_bounded(&full[i], 0, kDrainLimitNs);
-  }
+  if (t == 0)
+    for (int64_t q = confirmed; q < issued; ++q)
+      mbar_wait_bounded(&full[q % NST], static_cast<uint32_t>((q / NST) & 1), kDrainLimitNs);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -439,7 +488,8 @@ cudaError_t launch_fixed_tma(const Batch& b, StagedShape shape, int num_sms,
   CUtensorMap tmap;
   cudaError_t e = encode_rows(b, &tmap, kRows);
   if (e != cudaSuccess) return e;
-  FixedParams p{b.n, b.fixed_len, b.keys, b.per_message_keys, b.out, b.words, b.err, 1u};
+  FixedParams p{b.n, b.fixed_len, b.keys, b.per_message_keys, b.out, b.words, b.err, 1u,
+                b.wait_ns};
 #define HH_FIXED(W_, N_, M_)                                          \
   if (shape.window == W_ && shape.stages == N_ && shape.msgs == M_) \
     return launch_fixed_t<W_, N_, M_>(tmap, p, num_sms, stream);
@@ -456,7 +506,8 @@ cudaError_t launch_fixed_tma_pair(const Batch& b, int num_sms, cudaStream_t stre
   CUtensorMap tmap;
   cudaError_t e = encode_rows(b, &tmap, rows);
   if (e != cudaSuccess) return e;
-  FixedParams p{b.n, b.fixed_len, b.keys, b.per_message_keys, b.out, b.words, b.err, 1u};
+  FixedParams p{b.n, b.fixed_len, b.keys, b.per_message_keys, b.out, b.words, b.err, 1u,
+                b.wait_ns};
   if (rows == 128) return launch_fixed_pair_t<256, 2, 128>(tmap, p, num_sms, stream);
   if (rows == 64) return launch_fixed_pair_t<256, 2, 64>(tmap, p, num_sms, stream);
   return launch_fixed_pair_t<256, 2, 32>(tmap, p, num_sms, stream);

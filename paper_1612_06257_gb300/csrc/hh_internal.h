@@ -13,6 +13,15 @@ constexpr int kErrBadOffsets = 6;   // also: a segment outside the buffer
 constexpr int kErrBadKey = 8;       // a key index outside the key table
 constexpr int kErrBadChunk = 9;     // a stream-update chunk not a multiple of 32 bytes
 
+// Bounds on the kernels' waits for asynchronous copies.  A wait that runs
+// past its limit records kErrTimeout; the kernel then stops issuing copies,
+// waits (at most kDrainLimitNs per copy) for the ones still in flight, and
+// writes zero hashes for what it could not finish.  The limit is a
+// per-context setting (hh_set_tune_param "wait_limit_ns"); 0 tests each
+// barrier once without blocking.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: far beyond any legitimate wait
+constexpr uint64_t kDrainLimitNs = 200000000ull;  // 0.2 s per copy when giving up
+
 // Length-sort buckets by the number of Updates P = ceil(len / 32) a message
 // needs before finalisation: P itself below 2048, then 128 buckets per
 // doubling of P (messages up to 4 GiB).  By default messages in kHugeBucket
@@ -51,6 +60,7 @@ struct Batch {
   int stream_mode;           // kWholeMessages, kStreamUpdate or kStreamFinish
   int* err;                  // device error word (first error wins)
   uint64_t* states;          // streams: n x 16 words (v0, v1, mul0, mul1; lanes 0..3)
+  uint64_t wait_ns = kWaitLimitNs;  // limit of one wait for an asynchronous copy
 };
 
 // What a batch's messages are: whole messages (Init from the key, hash

@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(kTileRows) staged_kernel(Batch b, Queue q) {
   int wait_buf = 0;                  // buffer of the next step to wait for
   uint32_t wait_parity = 0;          // phase parity of that buffer
   int in_flight = 0;                 // steps issued but not yet waited for
-  bool aborted = false;
+  bool aborted = false;  // a wait ran over the limit: no more copies or hashing
+  bool broken = false;   // a phase did not complete even within kDrainLimitNs
   int64_t static_tile = blockIdx.x;
 
   for (;;) {
@@ -236,9 +237,13 @@ __global__ void __launch_bounds__(kTileRows) staged_kernel(Batch b, Queue q) {
     for (int64_t k = 0; k < steps; ++k) {
       if (k + NST - 1 < steps) issue(k + NST - 1);
       const int buf = wait_buf;
-      if (!aborted && !mbar_wait_bounded(&bars[buf], wait_parity, kWaitLimitNs)) {
+      if (!broken && !mbar_wait_bounded(&bars[buf], wait_parity, b.wait_ns)) {
+        // Over the limit: record the timeout, stop copying and hashing, but
+        // keep waiting for this phase (bounded) so that every thread still
+        // arrives exactly once per phase and no phase completes early.
+        if (!aborted) record_error(b.err, kErrTimeout);
         aborted = true;
-        record_error(b.err, kErrTimeout);
+        if (!mbar_wait_bounded(&bars[buf], wait_parity, kDrainLimitNs)) broken = true;
       }
       wait_buf = (wait_buf + 1 == NST) ? 0 : wait_buf + 1;
       if (wait_buf == 0) wait_parity ^= 1u;
@@ -265,9 +270,10 @@ __global__ void __launch_bounds__(kTileRows) staged_kernel(Batch b, Queue q) {
     __syncthreads();  // s_tile and s_steps are rewritten for the next tile
   }
 
-  // After a timeout, give copies still in flight a bounded time to land
-  // before the CTA's shared memory is released.
-  while (in_flight > 0) {
+  // Phases issued but not yet waited for (only after a timeout) complete
+  // before the CTA's shared memory is released.  Only a copy that never
+  // lands (`broken`) can leave this loop early.
+  while (in_flight > 0 && !broken) {
     mbar_wait_bounded(&bars[wait_buf], wait_parity, kDrainLimitNs);
     wait_buf = (wait_buf + 1 == NST) ? 0 : wait_buf + 1;
     if (wait_buf == 0) wait_parity ^= 1u;

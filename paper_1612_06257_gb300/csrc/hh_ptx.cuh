@@ -6,6 +6,8 @@
 
 #include <cstdint>
 
+#include "hh_internal.h"
+
 namespace hh {
 
 // Record a device-side error code; the first one recorded wins.
@@ -72,10 +74,25 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Wait for a phase of an mbarrier, giving up after `limit_ns`.
+// Non-blocking test of a phase of an mbarrier.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for a phase of an mbarrier, giving up after `limit_ns` (0: one
+// non-blocking test).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   uint64_t limit_ns) {
   const uint32_t a = smem_u32(bar);
+  if (limit_ns == 0) return mbar_test_wait(a, parity);
   if (mbar_try_wait(a, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(a, parity)) {
@@ -83,9 +100,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
   return true;
 }
-
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: far beyond any legitimate wait
-constexpr uint64_t kDrainLimitNs = 200000000ull;  // 0.2 s per buffer when giving up
 
 // 128-bit shared-memory load (kept as one LDS.128; the address must be
 // 16-byte aligned).

@@ -342,6 +342,12 @@ int hh_tune_describe(hh_ctx* ctx, char* buf, int64_t buf_len) {
 
 int hh_set_tune_param(hh_ctx* ctx, const char* name, int value) {
   if (ctx == nullptr || name == nullptr) return HH_ERR_INVALID_ARG;
+  if (std::strcmp(name, "wait_limit_ns") == 0) {
+    // A property of the context, not of the tuning table (never saved).
+    if (value < 0) return HH_ERR_INVALID_ARG;
+    ctx->wait_limit_ns = static_cast<uint64_t>(value);
+    return HH_OK;
+  }
   return hh::set_tune_scalar(ctx->tune, name, value) ? HH_OK : HH_ERR_INVALID_ARG;
 }
 

@@ -1,0 +1,67 @@
+"""GPU test of the give-up path of the copy pipelines (no fault, no hang).
+
+The context's wait limit is set to 0, so every barrier wait for an
+asynchronous copy becomes one non-blocking test, which fails while a copy is
+still in flight: the kernel records HH_ERR_TIMEOUT, stops issuing copies,
+waits (bounded) for the copies it already issued, and writes zero hashes for
+what it did not finish.  The copies themselves still land within
+microseconds, so the drain returns.  The test checks the status, that every
+output is either zero or the oracle's hash (a message whose every wait
+succeeded is hashed correctly), and that the next call with the limit
+restored matches the oracle on every message.
+"""
+import numpy as np
+import pytest
+
+from paper_1612_06257_gb300 import hh, workloads
+from tests.helpers import as_u64, oracle_hashes
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+DEFAULT_LIMIT_NS = 2_000_000_000
+
+
+@pytest.fixture()
+def ctx():
+    from paper_1612_06257_gb300 import build
+    build.build()
+    c = hh.hh_init(0)
+    yield c
+    hh.hh_destroy(c)
+
+
+def _run(ctx, path, w):
+    if path == "bulk":
+        out = hh.hh_hash64_batch(ctx, w.keys, w.key_mode, w.data, w.offsets_or_stride())
+    else:
+        out = hh.hh_hash_fixed(ctx, 64, w.keys, w.key_mode, w.data, w.fixed_len, w.n)
+    return out
+
+
+@pytest.mark.parametrize("path", ["tma", "pair", "bulk"])
+def test_zero_wait_limit_gives_up_and_the_next_call_is_exact(ctx, path):
+    # 512 messages of 16 KiB: a small fixed batch, 64 windows per message.
+    w = workloads.fixed(512, 16384, seed=31, device=DEV)
+    if path == "tma":
+        hh.hh_set_tune_param(ctx, "fixed_pair", 0)  # one thread per message (TMA kernel)
+    elif path == "bulk":
+        hh.hh_set_kernel(ctx, hh.HH_KERNEL_STAGED_BULK)  # per-thread bulk copies
+    expect = oracle_hashes(w, 64)
+    hh.hh_set_tune_param(ctx, "wait_limit_ns", 0)
+    out = _run(ctx, path, w)
+    assert hh.hh_get_device_error(ctx) == hh.HH_ERR_TIMEOUT
+    got = as_u64(out, 1)
+    zero = got[:, 0] == 0
+    assert zero.any()
+    assert np.array_equal(got[~zero], expect[~zero])
+    hh.hh_set_tune_param(ctx, "wait_limit_ns", DEFAULT_LIMIT_NS)
+    out = _run(ctx, path, w)
+    assert hh.hh_get_device_error(ctx) == hh.HH_OK
+    assert np.array_equal(as_u64(out, 1), expect)
+
+
+def test_wait_limit_rejects_negative_values(ctx):
+    L = hh.load_library()
+    assert L.hh_set_tune_param(ctx.ptr, b"wait_limit_ns", -1) == hh.HH_ERR_INVALID_ARG
+    assert L.hh_set_tune_param(ctx.ptr, b"wait_limit_ns", 1000) == hh.HH_OK

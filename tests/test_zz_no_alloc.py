@@ -4,8 +4,12 @@ It is for callers that cannot allocate device memory for this library (their
 memory belongs to another allocator or a fixed budget, or they cannot afford
 cudaMalloc's implicit synchronisation).  The test calls it through the C ABI
 twice in a row, on two different batches, and requires each result to equal
-hh_hash_batch's for the same batch word for word (the tolerance of every hash
-test: zero).  It also checks the size limit.  This file is collected last.
+hh_hash_batch's for the same batch and the CPU oracle's, word for word (the
+tolerance of every hash test: zero).  Further cases reach the messages of
+128 KiB and more (one warp or two threads per message) with 128-bit output,
+and a batch of exactly the limit's 2^20 messages, checked on a sample
+against the oracle.  It also checks the size limit.  This file is collected
+last.
 """
 import ctypes
 
@@ -14,6 +18,7 @@ import pytest
 import torch
 
 from paper_1612_06257_gb300 import hh, workloads
+from tests.helpers import as_u64, oracle_hashes
 
 pytestmark = pytest.mark.gpu
 
@@ -55,8 +60,50 @@ def test_noalloc_matches_batch_entry_point_twice():
             torch.cuda.synchronize()
             assert int(err.item()) == hh.HH_OK
             assert np.array_equal(out.cpu().numpy(), expect.cpu().numpy())
+            assert np.array_equal(as_u64(out, words), oracle_hashes(w, bits))
     finally:
         hh.hh_destroy(ctx)
+
+
+def test_noalloc_long_messages_128_bit():
+    """Messages of 128 KiB and more come first in the length order and run
+    one per warp or two threads each; 128-bit output."""
+    lib = hh.load_library()
+    ctx = hh.hh_init(0)
+    try:
+        g = torch.Generator().manual_seed(79)
+        lengths = torch.cat([torch.randint(0, 3000, (2000,), generator=g),
+                             torch.tensor([(1 << 17), (1 << 17) + 5, 300001, (1 << 20) + 31]),
+                             torch.randint(1 << 17, 1 << 19, (40,), generator=g)])
+        lengths = lengths[torch.randperm(lengths.numel(), generator=g)]
+        w = workloads.from_lengths(lengths, seed=79, device=DEV, per_message_keys=True)
+        expect = hh.hh_hash128_batch(ctx, w.keys, w.key_mode, w.data, w.offsets)
+        assert hh.hh_get_device_error(ctx) == hh.HH_OK
+        out = torch.full((w.n * 2,), -1, dtype=torch.int64, device=DEV)
+        err = torch.zeros(1, dtype=torch.int32, device=DEV)
+        assert _noalloc(lib, 128, w, out, err) == hh.HH_OK
+        torch.cuda.synchronize()
+        assert int(err.item()) == hh.HH_OK
+        assert np.array_equal(out.cpu().numpy(), expect.cpu().numpy())
+        assert np.array_equal(as_u64(out, 2), oracle_hashes(w, 128))
+    finally:
+        hh.hh_destroy(ctx)
+
+
+def test_noalloc_at_its_message_limit():
+    """Exactly 2^20 ragged messages (the sort's multi-block path over the
+    whole static array), sampled against the oracle, both ends included."""
+    lib = hh.load_library()
+    w = workloads.ragged(1 << 20, seed=80, device=DEV, max_len=4096)
+    out = torch.full((w.n,), -1, dtype=torch.int64, device=DEV)
+    err = torch.zeros(1, dtype=torch.int32, device=DEV)
+    assert _noalloc(lib, 64, w, out, err) == hh.HH_OK
+    torch.cuda.synchronize()
+    assert int(err.item()) == hh.HH_OK
+    rng = np.random.default_rng(80)
+    idx = np.unique(np.concatenate([rng.choice(w.n, 3000, replace=False), [0, 1, w.n - 2, w.n - 1]]))
+    got = as_u64(out, 1)
+    assert np.array_equal(got[idx], oracle_hashes(w, 64, indices=idx))
 
 
 def test_noalloc_rejects_batches_beyond_its_limit():
