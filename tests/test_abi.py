@@ -112,7 +112,7 @@ def test_product_and_oracle_share_no_code():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 for pattern in (r"\bimport oracle\b", r"\bfrom oracle\b", r"\bhho_",
-                                r"hho\.h", r"liboracle"):
+                                r"hho\.h", r"liboracle", r"\bsipo_", r"sipo\.h"):
                     assert not re.search(pattern, text), (f, pattern)
     odir = os.path.join(ROOT, "oracle")
     for f in os.listdir(odir):
@@ -120,3 +120,4 @@ def test_product_and_oracle_share_no_code():
             text = open(os.path.join(odir, f)).read()
             assert "hh_device" not in text and "import paper_1612_06257_gb300" not in text
             assert "#include \"hh.h\"" not in text
+            assert "siptree.cuh" not in text and "hh_internal" not in text
