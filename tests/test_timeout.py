@@ -9,9 +9,15 @@ microseconds, so the drain returns.  The test checks the status, that every
 output is either zero or the oracle's hash (a message whose every wait
 succeeded is hashed correctly), and that the next call with the limit
 restored matches the oracle on every message.
+
+The per-thread bulk-copy kernel (HH_KERNEL_STAGED_BULK) issues its copies
+one lane at a time, slowly enough that a copy has often landed by the time
+its barrier is tested, so there a give-up is likely but not certain: that
+case accepts either status, and checks the same zero-or-exact property.
 """
 import numpy as np
 import pytest
+import torch
 
 from paper_1612_06257_gb300 import hh, workloads
 from tests.helpers import as_u64, oracle_hashes
@@ -49,11 +55,17 @@ def test_zero_wait_limit_gives_up_and_the_next_call_is_exact(ctx, path):
         hh.hh_set_kernel(ctx, hh.HH_KERNEL_STAGED_BULK)  # per-thread bulk copies
     expect = oracle_hashes(w, 64)
     hh.hh_set_tune_param(ctx, "wait_limit_ns", 0)
+    torch.empty(512 << 20, dtype=torch.uint8, device=DEV).fill_(1)  # inputs out of L2
     out = _run(ctx, path, w)
-    assert hh.hh_get_device_error(ctx) == hh.HH_ERR_TIMEOUT
+    status = hh.hh_get_device_error(ctx)
     got = as_u64(out, 1)
     zero = got[:, 0] == 0
-    assert zero.any()
+    if path == "bulk":
+        assert status in (hh.HH_OK, hh.HH_ERR_TIMEOUT)
+        assert zero.any() == (status == hh.HH_ERR_TIMEOUT)
+    else:
+        assert status == hh.HH_ERR_TIMEOUT
+        assert zero.any()
     assert np.array_equal(got[~zero], expect[~zero])
     hh.hh_set_tune_param(ctx, "wait_limit_ns", DEFAULT_LIMIT_NS)
     out = _run(ctx, path, w)
