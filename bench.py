@@ -48,8 +48,11 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extra-configs", action="store_true",
+                   help="skip the ragged, short and SipTreeHash figures (extra.*)")
     p.add_argument("--workload", default=None,
-                   choices=["small", "ragged", "short", "serving", "prng", "stats", "oracle"],
+                   choices=["small", "ragged", "short", "serving", "prng", "stats", "siptree",
+                            "oracle"],
                    help="measure another batch shape instead (one JSON line; not the "
                         "headline step)")
     return p.parse_args()
@@ -428,6 +431,24 @@ def run_ours(args, rank, world, local_rank):
            "d2h_bytes_per_step": 8 * N_MESSAGES,
            "api": "hh_hash_host (pinned host buffers, chunked H2D/hash/D2H)",
            "h2d_copy_gbs": round(payload / min(copy_s) / 1e9, 1)}
+
+    # The other configurations of the same metric, each with its own clock
+    # record: config 3 (2^22 log-uniform ragged messages, per-message keys:
+    # HBM roofline), config 4 (2^26 messages of 0..64 B: integer-issue
+    # roofline), and SipTreeHash beside HighwayHash on this batch.
+    if not args.no_extra_configs:
+        from paper_1612_06257_gb300 import bench_workloads
+        torch.cuda.empty_cache()
+        for name, fn in (("ragged", lambda: bench_workloads.ragged(ctx, dev, naive_reps=1)),
+                         ("short", lambda: bench_workloads.short(ctx, dev)),
+                         ("siptree", lambda: bench_workloads.siptree(ctx, dev, w))):
+            s = ClockSampler(local_rank)
+            s.start()
+            res = fn()
+            s.stop()
+            res["clocks"] = s.summary()
+            extra[name] = res
+            torch.cuda.empty_cache()
 
     result = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,

@@ -218,6 +218,24 @@ int hh_hash_batch_noalloc(int bits, const uint64_t* keys, int key_mode, const ui
                           void* stream);
 
 /*
+ * SipTreeHash (Section 3), the paper's tree extension of SipHash, of a ragged
+ * batch; 64-bit output.  Same keys, bytes, offsets, n and out conventions,
+ * errors and asynchrony as hh_hash64_batch (and the same scratch limit);
+ * `variant` is HH_SIPTREE (SipHash-2-4 lanes) or HH_SIPTREE13 (SipHash-1-3,
+ * Section 5).  Section 3 fixes four interleaved SipHash lanes over 64-bit
+ * words whose results are hashed again; the rest is read as follows: the
+ * message is zero-padded to P = ceil(len / 32) vectors of 32 bytes; little-
+ * endian word i goes to lane i mod 4; lane j is the standard SipHash of its
+ * 8P bytes; the result is the standard SipHash of the four lane results
+ * followed by len (five little-endian words); every SipHash is keyed with
+ * key words 0 and 1 (words 2 and 3 are not used).
+ */
+enum hh_siptree_variant { HH_SIPTREE = 24, HH_SIPTREE13 = 13 };
+int hh_siptree_batch(hh_ctx* ctx, int variant, const uint64_t* keys, int key_mode,
+                     const uint8_t* bytes, const int64_t* offsets, int64_t n, uint64_t* out,
+                     void* stream);
+
+/*
  * Synchronise `stream`, then return and clear the context's device error
  * word: HH_OK, HH_ERR_BAD_OFFSETS, HH_ERR_BAD_KEY_INDEX, HH_ERR_BAD_CHUNK or
  * HH_ERR_TIMEOUT (the first one recorded).

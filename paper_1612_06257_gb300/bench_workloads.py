@@ -13,6 +13,8 @@
            latency at Poisson arrival rates swept over 0.1-0.9 of it.
   prng     2^28 counter-mode 64-bit words (hh_prng_fill): words/s against
            the integer ceiling (5 Updates per word).
+  siptree  SipTreeHash and SipTreeHash13 (Section 3) beside HighwayHash on
+           2^20 x 1 KiB through the offsets form: GB/s of each.
   stats    the paper's statistical studies on the GPU: toggle bias of all
            2^24 three-byte inputs after 2, 3 and 4 finalisation rounds, and
            the avalanche test for sizes 4-32 (49 samples, 1M iterations).
@@ -116,21 +118,24 @@ def small(ctx, dev):
             "note": "4 MiB fits L2; 4096 messages, two threads each, in 32-row tiles on 128 of 152 SMs: a latency regime bound by each thread's Update chain"}
 
 
-def ragged(ctx, dev):
+def ragged(ctx, dev, naive_reps=3):
     w = workloads.ragged(1 << 22, seed=2, device=dev)
     out = torch.empty(w.n, dtype=torch.int64, device=dev)
     fn = lambda: hh.hh_hash64_batch(ctx, w.keys, 1, w.data, w.offsets, out=out)  # noqa: E731
     ms, _ = _time(fn, 10)
     launches = hh.hh_last_launch_count(ctx)
-    naive = _naive_ms(ctx, fn, 3)
+    naive = _naive_ms(ctx, fn, naive_reps)
     alg = w.total_bytes + 8 * (w.n + 1) + 32 * w.n + 8 * w.n
     peak, kind = _peak_hbm()
-    return {"workload": "2^22 messages, log-uniform lengths in [0, 65536], per-message keys, "
-                        "64-bit", "bytes": w.total_bytes, "ms_per_batch": round(ms, 3),
+    return {"workload": "2^22 messages, log-uniform lengths in [0, 65536] (every residue mod 32), "
+                        "per-message keys, 64-bit", "bytes": w.total_bytes, "ms_per_batch": round(ms, 3),
             "gbps": round(w.total_bytes / ms / 1e6, 1), "hashes_per_s": round(w.n / ms * 1e3, 1),
             "roofline": {"bound": "hbm", "achieved": round(alg / ms / 1e6, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(alg / ms / 1e6 / peak, 4),
-                         "peak_source": kind, "algorithmic_bytes": alg},
+                         "peak_source": kind, "algorithmic_bytes": alg,
+                         "algorithmic_bytes_formula": "sum(len) + 8(n+1) offsets + 32n keys + 8n out",
+                         "timing": "median of 10 launches, each between CUDA events; inputs "
+                                   "(25 GB) larger than L2"},
             "launches_per_batch": launches,
             "naive_gbps": round(w.total_bytes / naive / 1e6, 1),
             "speedup_vs_naive": round(naive / ms, 2)}
@@ -156,13 +161,16 @@ def short(ctx, dev):
     ceiling = _update_ceiling(ctx, dev) / upd_per_hash
     res = {"workload": "2^26 messages of 0..64 B (10% all zero), one key",
            "updates_per_hash": round(upd_per_hash, 3),
-           "integer_ceiling_hashes_per_s": round(ceiling, 1)}
+           "integer_ceiling_hashes_per_s": round(ceiling, 1),
+           "integer_ceiling": "Update microbenchmark (register state, no memory) measured in "
+                              "this run, divided by the Updates per hash"}
     for bits, fn in ((64, hh.hh_hash64_batch), (128, hh.hh_hash128_batch)):
         out = torch.empty(w.n * bits // 64, dtype=torch.int64, device=dev)
         ms, _ = _time(lambda: fn(ctx, w.keys, 0, w.data, w.offsets, out=out), 10)
         hps = w.n / (ms / 1e3)
         res["hashes_per_s_%d" % bits] = round(hps, 1)
         res["integer_frac_%d" % bits] = round(hps / ceiling, 4)
+        res["launches_per_batch_%d" % bits] = hh.hh_last_launch_count(ctx)
         res["gbps_%d" % bits] = round(w.total_bytes / ms / 1e6, 1)
         if bits == 64:
             naive = _naive_ms(ctx, lambda: fn(ctx, w.keys, 0, w.data, w.offsets, out=out), 5)
@@ -206,6 +214,34 @@ def serving(ctx, dev, requests=64, pool_gib=8, rates=(0.1, 0.3, 0.5, 0.7, 0.9)):
             "sweep": sweep, "device_errors": errors}
 
 
+def siptree(ctx, dev, w=None):
+    """SipTreeHash and SipTreeHash13 (Section 3) beside HighwayHash on one
+    batch through the same offsets form (Table 1 compares them on one CPU
+    core; here on one GB300): by default the benchmark's 2^20 x 1 KiB batch."""
+    if w is None:
+        w = workloads.fixed(1 << 20, 1024, seed=1000, device=dev)
+    offsets = w.offsets_or_stride()
+    out = torch.empty(w.n, dtype=torch.int64, device=dev)
+    res = {"workload": "%d messages x %d B, one key, 64-bit, offsets form" % (w.n, w.fixed_len or 0)}
+    fns = {"highwayhash": lambda: hh.hh_hash64_batch(ctx, w.keys, w.key_mode, w.data, offsets,
+                                                      out=out),
+           "siptree": lambda: hh.hh_siptree_batch(ctx, hh.HH_SIPTREE, w.keys, w.key_mode, w.data,
+                                                  offsets, out=out),
+           "siptree13": lambda: hh.hh_siptree_batch(ctx, hh.HH_SIPTREE13, w.keys, w.key_mode,
+                                                    w.data, offsets, out=out)}
+    for name, fn in fns.items():
+        ms, _ = _time(fn, 10)
+        res["%s_gbps" % name] = round(w.total_bytes / ms / 1e6, 1)
+        res["%s_ms" % name] = round(ms, 4)
+    res["highwayhash_over_siptree"] = round(res["highwayhash_gbps"] / res["siptree_gbps"], 2)
+    res["highwayhash_over_siptree13"] = round(res["highwayhash_gbps"] / res["siptree13_gbps"], 2)
+    # Table 1 at 1024 B (cycles per byte on one Haswell core): SipTreeHash
+    # 0.57, SipTreeHash13 0.33, HighwayHash (AVX2) 0.24.
+    res["paper_cpu_ratio_at_1k"] = {"highwayhash_over_siptree": round(0.57 / 0.24, 2),
+                                    "highwayhash_over_siptree13": round(0.33 / 0.24, 2)}
+    return res
+
+
 def prng(ctx, dev):
     n = 1 << 28
     key = workloads.random_u64((4,), workloads.generator(9, dev), dev)
@@ -236,7 +272,7 @@ def stats_study(ctx, dev):
 
 
 WORKLOADS = {"small": small, "ragged": ragged, "short": short, "serving": serving, "prng": prng,
-             "stats": stats_study}
+             "stats": stats_study, "siptree": siptree}
 
 
 def run(name: str) -> dict:

@@ -370,6 +370,47 @@ int hh_hash_segments(hh_ctx* ctx, int bits, const uint64_t* key_table, int32_t k
   return hash_device(ctx, b, static_cast<cudaStream_t>(stream));
 }
 
+int hh_siptree_batch(hh_ctx* ctx, int variant, const uint64_t* keys, int key_mode,
+                     const uint8_t* bytes, const int64_t* offsets, int64_t n, uint64_t* out,
+                     void* stream) {
+  if (ctx == nullptr || (variant != HH_SIPTREE && variant != HH_SIPTREE13) ||
+      (key_mode != HH_KEY_SHARED && key_mode != HH_KEY_PER_MESSAGE) || n < 0)
+    return HH_ERR_INVALID_ARG;
+  ctx->last_launches = 0;
+  if (n == 0) return HH_OK;
+  if (keys == nullptr || bytes == nullptr || offsets == nullptr || out == nullptr)
+    return HH_ERR_INVALID_ARG;
+  if (n > ctx->perm_cap) return HH_ERR_TOO_LARGE;
+  DeviceGuard guard(ctx->device);
+  if (!guard.ok) return HH_ERR_CUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  hh::Batch b{};
+  b.bytes = bytes;
+  b.offsets = offsets;
+  b.keys = keys;
+  b.per_message_keys = key_mode == HH_KEY_PER_MESSAGE;
+  b.n = n;
+  b.out = out;
+  b.words = 1;
+  b.err = ctx->d_err;
+  b.wait_ns = ctx->wait_limit_ns;
+  // Longest first, as for HighwayHash; no message is set apart as huge.
+  int launches = 0;
+  cudaError_t e = hh::launch_bucket_sort(b, ctx->d_hist, ctx->d_cursor, ctx->d_perm,
+                                         ctx->d_next_tile, ctx->d_use_perm, ctx->d_huge,
+                                         hh::kBuckets, ctx->num_sms, s, &launches);
+  if (e != cudaSuccess) return to_status(e);
+  hh::Queue q{};
+  q.perm = ctx->d_perm;
+  q.use_perm = ctx->d_use_perm;
+  q.next_tile = ctx->d_next_tile;
+  q.tiles = (n + 31) / 32;
+  e = hh::launch_siptree(b, q, variant == HH_SIPTREE ? hh::kSipTree24 : hh::kSipTree13,
+                         ctx->num_sms, s);
+  ctx->last_launches = launches + 1;
+  return to_status(e);
+}
+
 int hh_stream_init(hh_ctx* ctx, const uint64_t* keys, int key_mode, int64_t n,
                    uint64_t* states, void* stream) {
   if (ctx == nullptr || n < 0 || (key_mode != HH_KEY_SHARED && key_mode != HH_KEY_PER_MESSAGE))

@@ -17,19 +17,24 @@
 // the TMA unit; they are never hashed.
 //
 // Giving up (a barrier wait that runs past the context's limit) is
-// CTA-wide.  The thread that gives up sets a shared flag before its warp
-// arrives on the "empty" barrier; every thread reads the flag before each
-// wait and from then on neither waits nor hashes, and writes zero hashes.
-// Thread 0 refills a buffer only after it has itself seen the buffer's
-// previous load land and, after the "empty" wait, found the flag clear; so
-// at most one load per buffer is ever in flight, no "full" phase is armed
-// twice, and no buffer is overwritten after the flag is set (a warp that
-// raced ahead after giving up can complete an "empty" phase early, but only
-// after setting the flag, which the refill check then sees).  Thread 0
-// counts the loads it issued and the prefix of them it saw land; before the
-// CTA exits it waits (kDrainLimitNs each) for every load of the difference,
-// load q on buffer q mod NST at phase parity (q / NST) mod 2, so no bulk copy
-// is still writing shared memory when the CTA's shared memory is released.
+// CTA-wide and keeps the barrier protocol intact:
+//  - the thread that gives up sets a shared flag; a thread whose wait is
+//    still blocked reads the flag (only in the blocked path) and gives up
+//    too.  A thread that gave up neither waits nor hashes, and writes zero
+//    hashes; a thread whose every wait succeeded hashed landed data.
+//  - a warp arrives on an "empty" barrier only while some lane of it is
+//    still live, so a warp whose lanes all gave up (and no longer wait) never
+//    races ahead into a later phase: every "empty" phase completes only when
+//    every warp has really finished reading that buffer, and a refill never
+//    overwrites data still being read.
+//  - thread 0 refills a buffer only after it has itself seen the buffer's
+//    previous load land, so at most one load per buffer is in flight and no
+//    "full" phase is armed twice.
+//  - thread 0 counts the loads it issued and the prefix of them it saw
+//    land; before the CTA exits it waits (kDrainLimitNs each) for every load
+//    of the difference, load q on buffer q mod NST at phase parity
+//    (q / NST) mod 2, so no bulk copy still writes shared memory when the
+//    CTA's shared memory is released.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -43,6 +48,7 @@ namespace hh {
 namespace {
 
 constexpr int kRows = 128;           // messages per tile = box height = threads
+constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kBoxBytes = 128 * kRows;
 
 struct FixedParams {
@@ -57,8 +63,8 @@ struct FixedParams {
   uint64_t wait_ns;  // limit of one barrier wait (0: a single non-blocking test)
 };
 
-// Give up on the pipeline: every thread of the CTA stops waiting and hashing
-// once it sees the flag, and the producer issues no further load.
+// Give up on the pipeline: record the timeout and raise the CTA's flag, which
+// every thread still blocked in a wait then sees.
 __device__ __forceinline__ void give_up(volatile int* flag, int* err) {
   *flag = 1;
   __threadfence_block();
@@ -166,11 +172,10 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
     }
     for (int64_t k = 0; k < steps; ++k, ++g) {
       if (ok) {
-        if (*abort_flag != 0) {
+        const int w = mbar_wait_or_flag(&full[b], parity, p.wait_ns, abort_flag);
+        if (w != kWaitDone) {
           ok = false;
-        } else if (!mbar_wait_bounded(&full[b], parity, p.wait_ns)) {
-          ok = false;
-          give_up(abort_flag, p.err);
+          if (w == kWaitTimedOut) give_up(abort_flag, p.err);
         }
       }
       const uint8_t* stage = smem + b * L::kStageBytes;
@@ -198,17 +203,18 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[b]);
+      const bool live = __any_sync(kFullMask, ok);
+      if (lane == 0 && live) mbar_arrive(&empty[b]);
       if (t == 0 && ok) {
         confirmed = g + 1;  // this thread saw load g land
         if (g + NST < total) {
-          // Refill this buffer once every warp has read it, unless some
-          // thread has given up.
-          if (!mbar_wait_bounded(&empty[b], parity, p.wait_ns)) {
-            give_up(abort_flag, p.err);
-          } else if (*abort_flag == 0) {
+          // Refill this buffer once every warp has read it.
+          const int w = mbar_wait_or_flag(&empty[b], parity, p.wait_ns, abort_flag);
+          if (w == kWaitDone) {
             fence_proxy_async_smem();
             issue_next();
+          } else if (w == kWaitTimedOut) {
+            give_up(abort_flag, p.err);
           }
         }
       }
@@ -333,11 +339,10 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
     init_half(s, key, half);
     for (int64_t k = 0; k < steps; ++k, ++g) {
       if (ok) {
-        if (*abort_flag != 0) {
+        const int w = mbar_wait_or_flag(&full[b], parity, p.wait_ns, abort_flag);
+        if (w != kWaitDone) {
           ok = false;
-        } else if (!mbar_wait_bounded(&full[b], parity, p.wait_ns)) {
-          ok = false;
-          give_up(abort_flag, p.err);
+          if (w == kWaitTimedOut) give_up(abort_flag, p.err);
         }
       }
       const uint8_t* stage = smem + b * L::kStageBytes;
@@ -361,15 +366,17 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[b]);
+      const bool live = __any_sync(kFullMask, ok);
+      if (lane == 0 && live) mbar_arrive(&empty[b]);
       if (t == 0 && ok) {
         confirmed = g + 1;  // this thread saw load g land
         if (g + NST < total) {
-          if (!mbar_wait_bounded(&empty[b], parity, p.wait_ns)) {
-            give_up(abort_flag, p.err);
-          } else if (*abort_flag == 0) {
+          const int w = mbar_wait_or_flag(&empty[b], parity, p.wait_ns, abort_flag);
+          if (w == kWaitDone) {
             fence_proxy_async_smem();
             issue_next();
+          } else if (w == kWaitTimedOut) {
+            give_up(abort_flag, p.err);
           }
         }
       }

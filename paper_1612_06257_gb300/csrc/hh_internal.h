@@ -136,6 +136,14 @@ cudaError_t launch_fixed_tma(const Batch& b, StagedShape shape, int num_sms, cud
 cudaError_t launch_fixed_tma_pair(const Batch& b, int num_sms, cudaStream_t stream);
 bool fixed_shape_valid(StagedShape shape);
 
+// SipTreeHash (Section 3) of an offsets or segments batch, 64-bit output,
+// one thread per message in warp tiles from q's order.  kSipTree24 runs
+// SipHash-2-4 lanes (SipTreeHash), kSipTree13 SipHash-1-3 (SipTreeHash13).
+constexpr int kSipTree24 = 0;
+constexpr int kSipTree13 = 1;
+cudaError_t launch_siptree(const Batch& b, const Queue& q, int variant, int num_sms,
+                           cudaStream_t stream);
+
 // Update-rate microbenchmark (threads must be a multiple of 256).
 cudaError_t launch_update_microbench(int variant, int64_t updates, int64_t threads,
                                      uint64_t* out, cudaStream_t stream);

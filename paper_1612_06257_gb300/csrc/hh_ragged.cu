@@ -6,17 +6,11 @@
 // Warps never wait on one another: no CTA barrier, a warp-private ring, and
 // warp tiles taken from a queue (longest first after the length sort).
 //
-// Loading a stage: a message's window is the 16-byte aligned span around
-// bytes [kW, kW + W) of it, in the row its lane owns.  Four lanes copy each
-// row, so one cp.async.cg
-// instruction moves 64 contiguous bytes of 8 rows (8 cache lines for 512
-// bytes); a row's base address and chunk range come from its owner lane by
-// shuffle, and chunk offsets fold into the instruction's immediate.  Only
-// the (at most two) partial 16-byte blocks at the two ends of the whole
-// batch are read bytewise, so no load leaves [offsets[0], offsets[n]).
-// When every row's window lies inside its message and its aligned span
-// inside the batch (all but the last window of long messages), the rows copy
-// all their chunks with no per-chunk tests.
+// Loading a stage (WarpStager, hh_stage.cuh): a message's window is the
+// 16-byte aligned span around bytes [kW, kW + W) of it, in the row its lane
+// owns; four lanes copy each row with 16-byte cp.async.cg, and only the
+// partial 16-byte blocks at the two ends of the whole batch are read
+// bytewise, so no load leaves [offsets[0], offsets[n]).
 //
 // Reading a packet: when every message of the warp tile starts 16-byte
 // aligned, two 128-bit shared loads; otherwise the nine enclosing 32-bit
@@ -35,70 +29,11 @@
 #include "hh_device.cuh"
 #include "hh_internal.h"
 #include "hh_ptx.cuh"
+#include "hh_stage.cuh"
 #include "hh_stream.cuh"
 
 namespace hh {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-template <int W, int NST>
-struct RaggedLayout {
-  static constexpr int kStride = W + 16;             // bytes per row
-  static constexpr int kChunks = kStride / 16;       // 16-byte chunks per row
-  static constexpr int kPerLane = (kChunks + 3) / 4; // chunks per lane per row
-  static constexpr int kStageBytes = 32 * kStride;
-  static constexpr int kWarpBytes = NST * kStageBytes + 64;  // + read-past pad
-  static_assert((kStride / 4) % 32 == 4, "row stride must rotate 128-bit banks");
-};
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-__device__ __forceinline__ int64_t warp_max(int64_t v) {
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    const int64_t o = __shfl_xor_sync(kFull, v, d);
-    v = o > v ? o : v;
-  }
-  return v;
-}
-
-template <bool kAligned>
-__device__ __forceinline__ void read_packet(const uint8_t* row, uint32_t off, uint32_t w[8]) {
-  if (kAligned) {
-    const uint4 a = lds128(row + off);
-    const uint4 c = lds128(row + off + 16);
-    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-    w[4] = c.x; w[5] = c.y; w[6] = c.z; w[7] = c.w;
-  } else {
-    const uint32_t* p = reinterpret_cast<const uint32_t*>(row + (off & ~3u));
-    const uint32_t sel = 0x3210u + 0x1111u * (off & 3u);
-    uint32_t x[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) x[i] = p[i];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) w[j] = __byte_perm(x[j], x[j + 1], sel);
-  }
-}
 
 // Hash the packets of step k that this lane's message has, from its row.
 template <int W, bool kAligned>
@@ -142,45 +77,13 @@ __device__ __forceinline__ void hash_step(State& s, const uint8_t* row, uint32_t
 }
 
 // Messages of at most 64 bytes (a whole warp of them), read straight from
-// global memory: at most 17 aligned 32-bit words per message, shifted into
-// place with one PRMT per word.  A message has at most two data Updates: a
-// whole first packet when len > 32, then its last packet (padded when
-// len mod 32 != 0).  So a warp runs at most two, whatever its length mix,
-// and the padded packet is built once per message.
-// [lo_b, hi_b) is the batch's byte range: words that cross its ends are read
-// bytewise so that no load leaves it.
-//
-// load_short_words reads the words into x[17]; hash_short_words hashes them
-// (b = msg & 3); hash_short does both.
-__device__ __forceinline__ void load_short_words(uint32_t x[17], uintptr_t msg, uint32_t len,
-                                                 uintptr_t lo_b, uintptr_t hi_b) {
-  const uintptr_t w0 = msg & ~uintptr_t(3);
-  const uint32_t b = static_cast<uint32_t>(msg & 3);
-  const uint32_t nwords = (b + len + 3) >> 2;  // <= 17
-  const uintptr_t lo4 = (lo_b + 3) & ~uintptr_t(3), hi4 = hi_b & ~uintptr_t(3);
-  if (w0 >= lo4 && w0 + 68 <= hi4) {
-    // All 17 words lie inside the batch: load them without per-word tests
-    // (words past the message are ignored below).
-#pragma unroll
-    for (int i = 0; i < 17; ++i) x[i] = __ldg(reinterpret_cast<const uint32_t*>(w0) + i);
-  } else if (w0 >= lo4 && w0 + 4 * nwords <= hi4) {
-#pragma unroll
-    for (int i = 0; i < 17; ++i)
-      x[i] = static_cast<uint32_t>(i) < nwords ? __ldg(reinterpret_cast<const uint32_t*>(w0) + i) : 0u;
-  } else {
-#pragma unroll
-    for (int i = 0; i < 17; ++i) {
-      uint32_t v = 0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uintptr_t p = w0 + 4 * i + k;
-        if (static_cast<uint32_t>(i) < nwords && p >= lo_b && p < hi_b)
-          v |= static_cast<uint32_t>(*reinterpret_cast<const uint8_t*>(p)) << (8 * k);
-      }
-      x[i] = v;
-    }
-  }
-}
+// global memory (load_short_words): at most 17 aligned 32-bit words per
+// message, shifted into place with one PRMT per word.  A message has at most
+// two data Updates: a whole first packet when len > 32, then its last packet
+// (padded when len mod 32 != 0).  So a warp runs at most two, whatever its
+// length mix, and the padded packet is built once per message.
+// hash_short_words hashes the words (b = msg & 3); hash_short loads and
+// hashes.
 
 // The last packet of a message from the eight words t that hold its last
 // len mod 32 (= r) bytes, padded as Section 4.5 asks: whole 4-byte groups
@@ -578,11 +481,6 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
   const uintptr_t safe_lo = (base + lo + 15) & ~uintptr_t(15);
   const uintptr_t safe_hi = (base + hi) & ~uintptr_t(15);
 
-  // Copy roles: lane = 4 * row_in_pass + part; pass h copies the windows of
-  // messages (lanes) 8h..8h+7.
-  const int part = lane & 3;
-  const int row_in_pass = lane >> 2;
-
   if (q.skip_if_short && q.use_perm != nullptr && *q.use_perm == 0) return;  // short kernel runs
   const int32_t* perm = (q.perm && (q.use_perm == nullptr || *q.use_perm)) ? q.perm : nullptr;
   // The huge prefix of the length order (messages perm[0 .. huge)) comes
@@ -693,119 +591,17 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
     const int64_t packets = len >> 5;
     const uint32_t r = static_cast<uint32_t>(len & 31);
     const int64_t rem_step = r ? (packets * 32) / W : -1;
-    // This lane's row in each stage.  Rows rotate the banks by 4 words, so
-    // rows q, q + 8, q + 16, q + 24 share four banks, and two of them
-    // conflict on an unaligned 32-bit load when their messages start at the
-    // same word of a 16-byte block.  Ranking the lanes by that word (mis / 4)
-    // and giving rank q row q spreads equal words over the eight groups.
-    int my_row = lane;
-    if (!aligned) {
-      const uint32_t word = valid ? (mis >> 2) : 0u;
-      const unsigned below = (1u << lane) - 1u;
-      int rank = 0;
-#pragma unroll
-      for (uint32_t v = 0; v < 4; ++v) {
-        const unsigned same = __ballot_sync(kFull, word == v);
-        if (v < word) rank += __popc(same);
-        if (v == word) rank += __popc(same & below);
-      }
-      my_row = rank;
-    }
-
-    // Stage k of all 32 messages into ring buffer (k % NST); message `lane`
-    // goes to row my_row.
-    auto issue = [&](int64_t k, int buf) {
-      // When every row's window lies inside its message and the row's whole
-      // 16-byte aligned span inside the batch, all rows copy every chunk
-      // (bytes past a window land in the row's slack and are never hashed).
-      const uintptr_t a0_full = (msg + static_cast<uintptr_t>(k) * W) & ~uintptr_t(15);
-      const bool row_full = k < my_steps && (k + 1) * W <= len && a0_full >= safe_lo &&
-                            a0_full + L::kStride <= safe_hi;
-      if (__all_sync(kFull, row_full)) {
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const int owner = 8 * h + row_in_pass;
-          const uintptr_t rbase = static_cast<uintptr_t>(
-              __shfl_sync(kFull, static_cast<unsigned long long>(a0_full), owner));
-          const int row = __shfl_sync(kFull, my_row, owner);
-          const char* src = reinterpret_cast<const char*>(rbase) + 16 * part;
-          const uint32_t dst = ring_s + buf * L::kStageBytes + row * L::kStride + 16 * part;
-#pragma unroll
-          for (int i = 0; i < L::kPerLane; ++i)
-            if (i + 1 < L::kPerLane || part + 4 * i < L::kChunks)
-              cp_async16(dst + 64 * i, src + 64 * i);
-        }
-        cp_async_commit();
-        return;
-      }
-      uint8_t* stage = ring + buf * L::kStageBytes;
-      // Owner side: this lane's window, as a 16-byte aligned chunk range.
-      uintptr_t a0 = 0;
-      uint32_t range = 0;  // first valid chunk | (end chunk << 8)
+    const WarpStager<W, NST> stager{ring, ring_s, msg, len, my_steps,
+                                    spread_row(aligned, valid, mis, lane), safe_lo, safe_hi,
+                                    lane};
+    stager.run(steps, [&](int64_t k, const uint8_t* row) {
       if (k < my_steps) {
-        const uintptr_t gs = msg + static_cast<uintptr_t>(k) * W;
-        const int64_t wend = k * W + W < len ? k * W + W : len;
-        const uintptr_t ge = msg + static_cast<uintptr_t>(wend);
-        a0 = gs & ~uintptr_t(15);
-        const uintptr_t a1 = (ge + 15) & ~uintptr_t(15);
-        const uintptr_t c0 = a0 > safe_lo ? a0 : safe_lo;
-        const uintptr_t c1 = a1 < safe_hi ? a1 : safe_hi;
-        uint32_t first = 0, end = 0;
-        if (c1 > c0) {
-          first = static_cast<uint32_t>((c0 - a0) >> 4);
-          end = static_cast<uint32_t>((c1 - a0) >> 4);
-        }
-        range = first | (end << 8);
-        if (c0 > gs || c1 < ge || c1 <= c0) {
-          // Bytes in the partial blocks at the batch ends: read bytewise.
-          uint8_t* row = stage + my_row * L::kStride;
-          for (uintptr_t p = gs; p < ge; ++p)
-            if (p < c0 || p >= c1 || c1 <= c0) row[p - a0] = *reinterpret_cast<const uint8_t*>(p);
-        }
-      }
-      // Copier side: four lanes per message, eight messages per pass.
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const int owner = 8 * h + row_in_pass;
-        const uintptr_t rbase = static_cast<uintptr_t>(
-            __shfl_sync(kFull, static_cast<unsigned long long>(a0), owner));
-        const uint32_t rr = __shfl_sync(kFull, range, owner);
-        const int row = __shfl_sync(kFull, my_row, owner);
-        const uint32_t first = rr & 0xff, end = rr >> 8;
-        const char* src = reinterpret_cast<const char*>(rbase) + 16 * part;
-        const uint32_t dst = ring_s + buf * L::kStageBytes + row * L::kStride + 16 * part;
-#pragma unroll
-        for (int i = 0; i < L::kPerLane; ++i) {
-          const uint32_t c = part + 4 * i;
-          if (c >= first && c < end) cp_async16(dst + 64 * i, src + 64 * i);
-        }
-      }
-      cp_async_commit();
-    };
-
-    int buf_issue = 0, buf_read = 0;
-    for (int64_t k = 0; k < NST - 1; ++k) {
-      if (k < steps) issue(k, buf_issue);
-      else cp_async_commit();
-      buf_issue = (buf_issue + 1 == NST) ? 0 : buf_issue + 1;
-    }
-    for (int64_t k = 0; k < steps; ++k) {
-      if (k + NST - 1 < steps) issue(k + NST - 1, buf_issue);
-      else cp_async_commit();
-      buf_issue = (buf_issue + 1 == NST) ? 0 : buf_issue + 1;
-      cp_async_wait<NST - 1>();
-      __syncwarp();
-      if (k < my_steps) {
-        const uint8_t* row = ring + buf_read * L::kStageBytes + my_row * L::kStride;
         if (aligned)  // warp-uniform
           hash_step<W, true>(s, row, 0u, k, packets, r, rem_step, 1u);
         else
           hash_step<W, false>(s, row, mis, k, packets, r, rem_step, 1u);
       }
-      __syncwarp();  // every lane is done with this buffer before it refills
-      buf_read = (buf_read + 1 == NST) ? 0 : buf_read + 1;
-    }
-    cp_async_wait<0>();
+    });
     end_state(b, m, valid, bad, s);
     __syncwarp();
   }

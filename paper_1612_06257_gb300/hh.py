@@ -53,8 +53,11 @@ EXPORTS = (
     "hh_update_microbench", "hh_hash_batch_noalloc", "hh_hash_segments", "hh_autotune",
     "hh_tune_save", "hh_tune_describe", "hh_set_tune_param", "hh_prng_fill",
     "hh_stats_round_table", "hh_stats_toggle_counts", "hh_stats_avalanche", "hh_stream_init",
-    "hh_stream_update", "hh_stream_finish",
+    "hh_stream_update", "hh_stream_finish", "hh_siptree_batch",
 )
+
+HH_SIPTREE = 24
+HH_SIPTREE13 = 13
 
 HH_REGIME_FIXED = 0
 HH_REGIME_RAGGED = 1
@@ -116,6 +119,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.hh_tune_describe.argtypes = [_vp, ctypes.c_char_p, _i64]
         L.hh_hash_segments.argtypes = [_vp, _int, _vp, ctypes.c_int32, _vp, _vp, _i64, _vp, _vp,
                                        _i64, _vp, _vp, _vp]
+        L.hh_siptree_batch.argtypes = [_vp, _int, _vp, _int, _vp, _vp, _i64, _vp, _vp]
         L.hh_status_string.argtypes = [_int]
         L.hh_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -213,6 +217,25 @@ def hh_hash128_batch(ctx, keys, key_mode, data, offsets, n=None, out=None, strea
 
 def hh_hash256_batch(ctx, keys, key_mode, data, offsets, n=None, out=None, stream=None):
     return _batch("hh_hash256_batch", 4, ctx, keys, key_mode, data, offsets, n, out, stream)
+
+
+def hh_siptree_batch(ctx, variant, keys, key_mode, data, offsets, n=None, out=None,
+                     stream=None):
+    """SipTreeHash (HH_SIPTREE) or SipTreeHash13 (HH_SIPTREE13) of a ragged
+    batch; returns out (int64 [n], uint64 bit patterns)."""
+    n = offsets.numel() - 1 if n is None else int(n)
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device=data.device)
+    if out.numel() < n:
+        raise ValueError("out holds %d words, need %d" % (out.numel(), n))
+    dev = ctx.device
+    st = load_library().hh_siptree_batch(
+        ctx.ptr, int(variant), _dev_ptr(keys, "keys", _I64, dev), int(key_mode),
+        _dev_ptr(data, "bytes", (torch.uint8,), dev),
+        _dev_ptr(offsets, "offsets", (torch.int64,), dev), n, _dev_ptr(out, "out", _I64, dev),
+        _stream_ptr(stream, dev))
+    _check(st, "hh_siptree_batch")
+    return out
 
 
 def hh_hash_fixed(ctx, bits, keys, key_mode, data, msg_len, n, out=None, stream=None):
