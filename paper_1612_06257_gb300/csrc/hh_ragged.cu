@@ -76,6 +76,49 @@ __device__ __forceinline__ void hash_step(State& s, const uint8_t* row, uint32_t
   }
 }
 
+// Two messages per lane, both with a full window at this step (a full window
+// never holds the remainder packet): their Update chains are independent, so
+// they run interleaved for twice the instruction-level parallelism.
+template <int W, bool kAligned>
+__device__ __forceinline__ void hash_full2(State& sa, const uint8_t* ra, uint32_t ma, State& sb,
+                                           const uint8_t* rb, uint32_t mb) {
+  if (kAligned) {
+#pragma unroll
+    for (int j = 0; j < W / 32; ++j) {
+      uint32_t wa[8], wb[8];
+      read_packet<true>(ra, 32u * j, wa);
+      read_packet<true>(rb, 32u * j, wb);
+      update_words_v<kFastUpdate>(sa, wa, 1u);
+      update_words_v<kFastUpdate>(sb, wb, 1u);
+    }
+  } else {
+    const uint32_t* pa = reinterpret_cast<const uint32_t*>(ra + (ma & ~3u));
+    const uint32_t* pb = reinterpret_cast<const uint32_t*>(rb + (mb & ~3u));
+    const uint32_t sela = 0x3210u + 0x1111u * (ma & 3u), selb = 0x3210u + 0x1111u * (mb & 3u);
+    uint32_t preva = pa[0], prevb = pb[0];
+#pragma unroll
+    for (int j = 0; j < W / 32; ++j) {
+      uint32_t xa[8], xb[8], wa[8], wb[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        xa[i] = pa[8 * j + 1 + i];
+        xb[i] = pb[8 * j + 1 + i];
+      }
+      wa[0] = __byte_perm(preva, xa[0], sela);
+      wb[0] = __byte_perm(prevb, xb[0], selb);
+#pragma unroll
+      for (int i = 1; i < 8; ++i) {
+        wa[i] = __byte_perm(xa[i - 1], xa[i], sela);
+        wb[i] = __byte_perm(xb[i - 1], xb[i], selb);
+      }
+      preva = xa[7];
+      prevb = xb[7];
+      update_words_v<kFastUpdate>(sa, wa, 1u);
+      update_words_v<kFastUpdate>(sb, wb, 1u);
+    }
+  }
+}
+
 // Messages of at most 64 bytes (a whole warp of them), read straight from
 // global memory (load_short_words): at most 17 aligned 32-bit words per
 // message, shifted into place with one PRMT per word.  A message has at most
@@ -466,9 +509,9 @@ __device__ __forceinline__ void solo_tile(const Batch& b, const int32_t* perm, i
   __syncwarp();
 }
 
-template <int W, int NST, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q) {
-  using L = RaggedLayout<W, NST>;
+template <int W, int NST, int WARPS, int M>
+__global__ void __launch_bounds__(WARPS * 32, M == 2 ? 3 : 2) ragged_kernel(Batch b, Queue q) {
+  using L = RaggedLayout<W, NST, M>;
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* ring = smem + warp * L::kWarpBytes;
@@ -486,7 +529,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
   // The huge prefix of the length order (messages perm[0 .. huge)) comes
   // first, then warp tiles of 32 messages from counter next_tile[0].
   const int64_t huge = (perm != nullptr && q.huge_count != nullptr) ? *q.huge_count : 0;
-  const int64_t tiles = (b.n - huge + 31) / 32;
+  const int64_t tiles = (b.n - huge + 32 * M - 1) / (32 * M);
   int64_t static_tile = static_cast<int64_t>(blockIdx.x) * WARPS + warp;
   const int64_t static_step = static_cast<int64_t>(gridDim.x) * WARPS;
 
@@ -567,42 +610,85 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
     }
     if (tile >= tiles) break;
 
-    const int64_t idx = huge + tile * 32 + lane;
-    const bool valid = idx < b.n;
-    int64_t m = 0, start = 0, len = 0;
-    int bad = 0;
-    if (valid) {
-      m = perm ? static_cast<int64_t>(perm[idx]) : idx;
-      message_bounds(b, m, start, len, bad);
-      if (bad) record_error(b.err, bad);
+    // Message i of this lane's tile slot: huge + tile * 32 M + 32 i + lane.
+    bool valid[M];
+    int64_t m[M], start[M], len[M];
+    int bad[M];
+    State s[M];
+    bool all_short = true;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const int64_t idx = huge + tile * 32 * M + 32 * i + lane;
+      valid[i] = idx < b.n;
+      m[i] = 0;
+      start[i] = 0;
+      len[i] = 0;
+      bad[i] = 0;
+      if (valid[i]) {
+        m[i] = perm ? static_cast<int64_t>(perm[idx]) : idx;
+        message_bounds(b, m[i], start[i], len[i], bad[i]);
+        if (bad[i]) record_error(b.err, bad[i]);
+      }
+      start_state(b, m[i], valid[i], s[i]);
+      all_short = all_short && len[i] <= 64;
     }
-    State s;
-    start_state(b, m, valid, s);
-    if (__all_sync(kFull, len <= 64)) {
-      hash_short(s, base + start, static_cast<uint32_t>(len), base + lo, base + hi);
-      end_state(b, m, valid, bad, s);
+    if (__all_sync(kFull, all_short)) {
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        hash_short(s[i], base + start[i], static_cast<uint32_t>(len[i]), base + lo, base + hi);
+        end_state(b, m[i], valid[i], bad[i], s[i]);
+      }
       continue;
     }
-    const int64_t my_steps = (len + W - 1) / W;
-    const int64_t steps = warp_max(my_steps);
-    const uintptr_t msg = base + start;
-    const uint32_t mis = static_cast<uint32_t>(msg & 15);
-    const bool aligned = __all_sync(kFull, mis == 0 || !valid);
-    const int64_t packets = len >> 5;
-    const uint32_t r = static_cast<uint32_t>(len & 31);
-    const int64_t rem_step = r ? (packets * 32) / W : -1;
-    const WarpStager<W, NST> stager{ring, ring_s, msg, len, my_steps,
-                                    spread_row(aligned, valid, mis, lane), safe_lo, safe_hi,
-                                    lane};
-    stager.run(steps, [&](int64_t k, const uint8_t* row) {
-      if (k < my_steps) {
+    int64_t my_steps[M], packets[M], rem_step[M];
+    uintptr_t msg[M];
+    uint32_t mis[M], r[M];
+    int64_t longest = 0;
+    bool all_aligned = true;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      my_steps[i] = (len[i] + W - 1) / W;
+      longest = my_steps[i] > longest ? my_steps[i] : longest;
+      msg[i] = base + start[i];
+      mis[i] = static_cast<uint32_t>(msg[i] & 15);
+      all_aligned = all_aligned && (mis[i] == 0 || !valid[i]);
+      packets[i] = len[i] >> 5;
+      r[i] = static_cast<uint32_t>(len[i] & 31);
+      rem_step[i] = r[i] ? (packets[i] * 32) / W : -1;
+    }
+    const int64_t steps = warp_max(longest);
+    const bool aligned = __all_sync(kFull, all_aligned);
+    WarpStager<W, NST, M> stager{ring, ring_s, {}, {}, {}, {}, safe_lo, safe_hi, lane};
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      stager.msg[i] = msg[i];
+      stager.len[i] = len[i];
+      stager.my_steps[i] = my_steps[i];
+      stager.my_row[i] = 32 * i + spread_row(aligned, valid[i], mis[i], lane);
+    }
+    stager.run(steps, [&](int64_t k, const uint8_t* stage) {
+      const uint8_t* row[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) row[i] = stage + stager.my_row[i] * L::kStride;
+      if (M == 2 && (k + 1) * (W / 32) <= packets[0] && (k + 1) * (W / 32) <= packets[M - 1]) {
         if (aligned)  // warp-uniform
-          hash_step<W, true>(s, row, 0u, k, packets, r, rem_step, 1u);
+          hash_full2<W, true>(s[0], row[0], 0u, s[M - 1], row[M - 1], 0u);
         else
-          hash_step<W, false>(s, row, mis, k, packets, r, rem_step, 1u);
+          hash_full2<W, false>(s[0], row[0], mis[0], s[M - 1], row[M - 1], mis[M - 1]);
+        return;
+      }
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        if (k < my_steps[i]) {
+          if (aligned)
+            hash_step<W, true>(s[i], row[i], 0u, k, packets[i], r[i], rem_step[i], 1u);
+          else
+            hash_step<W, false>(s[i], row[i], mis[i], k, packets[i], r[i], rem_step[i], 1u);
+        }
       }
     });
-    end_state(b, m, valid, bad, s);
+#pragma unroll
+    for (int i = 0; i < M; ++i) end_state(b, m[i], valid[i], bad[i], s[i]);
     __syncwarp();
   }
   // The last warp of a launch with huge messages leaves g_huge_kernels.
@@ -735,178 +821,11 @@ __global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, co
   }
 }
 
-// Offsets-form batches of messages of at most kShortMax bytes, whole
-// messages (the common case of the short kernel above, which keeps the
-// segments form and streams).  A block takes chunks of kChunk consecutive
-// messages; the chunk's offsets and then its bytes (at most kChunk * 64, one
-// contiguous range) are copied into shared memory with 8- and 16-byte
-// cp.async, the bytes one chunk ahead and the offsets two, so a message
-// waits for no global load.  Each chunk is then reordered, stable, into the
-// messages of at most 32 bytes (one data Update) followed by those of 33..64
-// bytes (two), so that every warp but one runs messages of one packet count
-// and no lane idles through an Update its message does not have.
-constexpr int kChunk = 256;
-constexpr int kChunkBytes = kChunk * kShortMax + 16;  // payload + alignment slack
-constexpr int kChunkPad = 80;                         // 17-word reads past the last start
-
-template <bool kPerMsgKeys>
-__global__ void __launch_bounds__(kChunk, 3) short_chunk_kernel(Batch b, const int* run_if) {
-  if (run_if != nullptr && *run_if != 0) return;
-  __shared__ __align__(16) uint8_t s_bytes[2][kChunkBytes + kChunkPad];
-  __shared__ __align__(16) int64_t s_offs[3][kChunk + 2];
-  __shared__ uint16_t s_order[kChunk];
-  __shared__ int s_count[2][kChunk / 32];  // per warp: messages of one, of two packets
-  resolve_count(b);
-  int64_t lo, hi;
-  batch_range(b, lo, hi);
-  const uintptr_t base = reinterpret_cast<uintptr_t>(b.bytes);
-  const uintptr_t lo_b = base + lo, hi_b = base + hi;
-  const uintptr_t safe_lo = (lo_b + 15) & ~uintptr_t(15), safe_hi = hi_b & ~uintptr_t(15);
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  uint64_t key[4];
-  if (!kPerMsgKeys) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) key[i] = __ldg(b.keys + i);
-  }
-  const int64_t chunks = (b.n + kChunk - 1) / kChunk;
-  const int64_t stride = gridDim.x;
-  auto count_of = [&](int64_t c) {
-    const int64_t left = b.n - c * kChunk;
-    return static_cast<int>(left < kChunk ? left : kChunk);
-  };
-  // Offsets c*kChunk .. c*kChunk + count into slot `o`.
-  auto stage_offsets = [&](int64_t c, int o) {
-    const int cnt = count_of(c);
-    const int64_t* src = b.offsets + c * kChunk;
-    if (t <= cnt) cp_async8(smem_u32(&s_offs[o][t]), src + t);
-    if (t == 0 && cnt == kChunk) cp_async8(smem_u32(&s_offs[o][kChunk]), src + kChunk);
-  };
-  // The chunk's byte range (from the offsets in slot o) into byte slot `y`:
-  // the 16-byte blocks inside the batch by cp.async, the partial blocks at
-  // the batch's ends bytewise.  Returns nothing; range_of gives the range.
-  auto range_of = [&](int o, int cnt, uintptr_t& a0, uintptr_t& c_lo, uintptr_t& c_hi) {
-    int64_t s0 = s_offs[o][0], s1 = s_offs[o][cnt];
-    s0 = s0 < lo ? lo : (s0 > hi ? hi : s0);
-    s1 = s1 < s0 ? s0 : (s1 > hi ? hi : s1);
-    c_lo = base + s0;
-    c_hi = base + s1;
-    a0 = c_lo & ~uintptr_t(15);
-    if (c_hi - a0 > static_cast<uintptr_t>(kChunkBytes)) c_hi = a0 + kChunkBytes;
-  };
-  auto stage_bytes = [&](int o, int cnt, int y) {
-    uintptr_t a0, c_lo, c_hi;
-    range_of(o, cnt, a0, c_lo, c_hi);
-    const int blocks = static_cast<int>((c_hi - a0 + 15) >> 4);
-    const uint32_t dst = smem_u32(&s_bytes[y][0]);
-    for (int k = t; k < blocks; k += kChunk) {
-      const uintptr_t p = a0 + 16 * static_cast<uintptr_t>(k);
-      if (p >= safe_lo && p + 16 <= safe_hi) {
-        cp_async16(dst + 16 * k, reinterpret_cast<const void*>(p));
-      } else {
-        for (int i = 0; i < 16; ++i)
-          if (p + i >= lo_b && p + i < hi_b)
-            s_bytes[y][16 * k + i] = *reinterpret_cast<const uint8_t*>(p + i);
-      }
-    }
-  };
-
-  int64_t c = blockIdx.x;
-  if (c >= chunks) return;
-  stage_offsets(c, 0);
-  cp_async_commit();
-  cp_async_wait<0>();
-  __syncthreads();
-  stage_bytes(0, count_of(c), 0);
-  if (c + stride < chunks) stage_offsets(c + stride, 1);
-  cp_async_commit();
-  int o = 0, y = 0;  // offsets slot and byte slot of chunk c
-  for (; c < chunks; c += stride) {
-    cp_async_wait<0>();
-    __syncthreads();  // chunk c's bytes and offsets, and the next chunk's offsets, are in
-    const int cnt = count_of(c);
-    const int64_t cn = c + stride;
-    const int o1 = o == 2 ? 0 : o + 1, o2 = o1 == 2 ? 0 : o1 + 1;
-    if (cn < chunks) {
-      stage_bytes(o1, count_of(cn), y ^ 1);
-      if (cn + stride < chunks) stage_offsets(cn + stride, o2);
-    }
-    cp_async_commit();
-
-    // Reorder: one-packet messages (and invalid ones) first, then two-packet.
-    bool two = false;
-    if (t < cnt) {
-      const int64_t s0 = s_offs[o][t], e0 = s_offs[o][t + 1];
-      two = e0 - s0 > 32;
-    }
-    const unsigned tw = __ballot_sync(kFull, two), one = __ballot_sync(kFull, !two && t < cnt);
-    if (lane == 0) {
-      s_count[0][warp] = __popc(one);
-      s_count[1][warp] = __popc(tw);
-    }
-    __syncthreads();
-    if (t < cnt) {
-      int before = 0, ones = 0;
-#pragma unroll
-      for (int w = 0; w < kChunk / 32; ++w) {
-        ones += s_count[0][w];
-        if (w < warp) before += two ? s_count[1][w] : s_count[0][w];
-      }
-      const unsigned mine = two ? tw : one;
-      const int pos = (two ? ones : 0) + before + __popc(mine & ((1u << lane) - 1u));
-      s_order[pos] = static_cast<uint16_t>(t);
-    }
-    __syncthreads();
-
-    if (t < cnt) {
-      const int j = s_order[t];
-      const int64_t m = c * kChunk + j;
-      const int64_t s0 = s_offs[o][j], e0 = s_offs[o][j + 1];
-      const int bad = e0 < s0 ? kErrBadOffsets : 0;
-      if (bad) record_error(b.err, bad);
-      int64_t len64 = bad ? 0 : e0 - s0;
-      const uint32_t len = static_cast<uint32_t>(len64 < kShortMax ? len64 : kShortMax);
-      if (kPerMsgKeys) {
-        const uint64_t* kp = b.keys + 4 * m;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
-      }
-      State st;
-      init(st, key);
-      uintptr_t a0, c_lo, c_hi;
-      range_of(o, cnt, a0, c_lo, c_hi);
-      const uintptr_t msg = base + s0;
-      uint32_t x[17];
-      if (!bad && msg >= c_lo && msg + len <= c_hi) {
-        // From the staged bytes (words past the message are don't-cares).
-        const uint32_t* p = reinterpret_cast<const uint32_t*>(
-            &s_bytes[y][((msg - a0) & ~uintptr_t(3))]);
-        if (len > 32u) {
-#pragma unroll
-          for (int i = 0; i < 17; ++i) x[i] = p[i];
-        } else {
-#pragma unroll
-          for (int i = 0; i < 9; ++i) x[i] = p[i];
-#pragma unroll
-          for (int i = 9; i < 17; ++i) x[i] = 0u;
-        }
-      } else {
-        // Only with decreasing offsets around: read from global memory.
-        load_short_words(x, bad ? lo_b : msg, len, lo_b, hi_b);
-      }
-      hash_short_words(st, x, static_cast<uint32_t>(msg & 3), len);
-      finalize(st);
-      store_short_hash(b, m, bad, st);
-    }
-    o = o1;
-    y ^= 1;
-  }
-}
-
-template <int W, int NST, int WARPS>
+template <int W, int NST, int WARPS, int M>
 cudaError_t launch_ragged_t(const Batch& b, const Queue& q, int num_sms, cudaStream_t stream) {
-  using L = RaggedLayout<W, NST>;
+  using L = RaggedLayout<W, NST, M>;
   constexpr int kBytes = WARPS * L::kWarpBytes;
-  auto kern = ragged_kernel<W, NST, WARPS>;
+  auto kern = ragged_kernel<W, NST, WARPS, M>;
   cudaError_t e;
   const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), WARPS * 32, kBytes, &e);
   if (e != cudaSuccess) return e;
@@ -921,18 +840,6 @@ cudaError_t launch_ragged_t(const Batch& b, const Queue& q, int num_sms, cudaStr
 }  // namespace
 
 cudaError_t launch_short(const Batch& b, const int* run_if, int num_sms, cudaStream_t stream) {
-  if (b.stream_mode == kWholeMessages && b.offsets != nullptr && b.key_index == nullptr) {
-    auto kern = b.per_message_keys ? short_chunk_kernel<true> : short_chunk_kernel<false>;
-    cudaError_t e;
-    const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), kChunk, 0, &e);
-    if (e != cudaSuccess) return e;
-    const int64_t blocks = (b.n + kChunk - 1) / kChunk;
-    const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
-    const int grid = static_cast<int>(blocks < cap ? blocks : cap);
-    if (grid <= 0) return cudaSuccess;
-    kern<<<grid, kChunk, 0, stream>>>(b, run_if);
-    return cudaGetLastError();
-  }
   auto kern = b.stream_mode != kWholeMessages ? short_kernel<true> : short_kernel<false>;
   cudaError_t e;
   const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), 256, 0, &e);
@@ -946,8 +853,8 @@ cudaError_t launch_short(const Batch& b, const int* run_if, int num_sms, cudaStr
 }
 
 bool ragged_shape_valid(StagedShape shape) {
-#define HH_VALID(W_, N_) \
-  if (shape.window == W_ && shape.stages == N_) return true;
+#define HH_VALID(W_, N_, M_) \
+  if (shape.window == W_ && shape.stages == N_ && shape.msgs == M_) return true;
   HH_RAGGED_SHAPES(HH_VALID)
 #undef HH_VALID
   return false;
@@ -955,8 +862,9 @@ bool ragged_shape_valid(StagedShape shape) {
 
 cudaError_t launch_ragged(const Batch& b, const Queue& q, StagedShape shape, int num_sms,
                           cudaStream_t stream) {
-#define HH_RAGGED(W_, N_) \
-  if (shape.window == W_ && shape.stages == N_) return launch_ragged_t<W_, N_, kRaggedWarps>(b, q, num_sms, stream);
+#define HH_RAGGED(W_, N_, M_)                                             \
+  if (shape.window == W_ && shape.stages == N_ && shape.msgs == M_)     \
+    return launch_ragged_t<W_, N_, kRaggedWarps, M_>(b, q, num_sms, stream);
   HH_RAGGED_SHAPES(HH_RAGGED)
 #undef HH_RAGGED
   return cudaErrorInvalidValue;
