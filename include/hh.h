@@ -272,10 +272,14 @@ int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages,
  * four-lane state in one thread and split the additions differently
  * between the ALU and FMA pipes; variants 6..11 are the same six splits for
  * one lane pair per thread (how messages of 128 KiB and more run).  The
- * variants of each group give identical output words.  With few threads it
- * measures the time of one Update chain rather than the pipes' throughput.
+ * variants of each group give identical output words.  Variant 12 keeps one
+ * lane per thread (four threads per state; thread 4s + q holds lane q, its
+ * packet word is its thread index, and it writes lane q of the output sum),
+ * trading the ZipperMerge partner's upper half by warp shuffle.  With few
+ * threads it measures the time of one Update chain rather than the pipes'
+ * throughput.
  */
-#define HH_UPDATE_VARIANTS 12
+#define HH_UPDATE_VARIANTS 13
 int hh_update_microbench(hh_ctx* ctx, int variant, int64_t updates, int64_t threads,
                          uint64_t* out, void* stream);
 

@@ -179,7 +179,7 @@ def short(ctx, dev):
     return res
 
 
-def serving(ctx, dev, requests=64, pool_gib=8, rates=(0.1, 0.3, 0.5, 0.7, 0.9)):
+def serving(ctx, dev, requests=512, pool_gib=8, rates=(0.1, 0.3, 0.5, 0.7, 0.9)):
     pool = workloads.random_bytes(pool_gib << 30, workloads.generator(7, dev), dev)
     specs = workloads.serving_requests(requests, pool.numel(), seed=8)
 
@@ -199,6 +199,7 @@ def serving(ctx, dev, requests=64, pool_gib=8, rates=(0.1, 0.3, 0.5, 0.7, 0.9)):
         for f in rates:
             st = serve.run_poisson(server, fresh(), rate_per_s=f * sat_rate, seed=2)
             sweep.append({"load": f, "rate_per_s": round(st["rate_per_s"], 2),
+                          "requests": st["requests"],
                           "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
                           "gbps": round(st["gbps"], 1)})
         errors = server.device_errors()
@@ -210,7 +211,9 @@ def serving(ctx, dev, requests=64, pool_gib=8, rates=(0.1, 0.3, 0.5, 0.7, 0.9)):
                         "(<= 4 requests per batch), 96 GiB in-flight cap" % requests,
             "bytes_per_pass": total,
             "saturation": {"gbps": round(sat["gbps"], 1), "requests_per_s": round(sat_rate, 2),
+                           "requests": sat["requests"],
                            "p50_ms": round(sat["p50_ms"], 2), "p99_ms": round(sat["p99_ms"], 2)},
+            "percentiles": "over every request of a load point (requests per point as listed)",
             "sweep": sweep, "device_errors": errors}
 
 

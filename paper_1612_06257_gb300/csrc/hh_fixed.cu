@@ -30,11 +30,12 @@
 //  - thread 0 refills a buffer only after it has itself seen the buffer's
 //    previous load land, so at most one load per buffer is in flight and no
 //    "full" phase is armed twice.
-//  - thread 0 counts the loads it issued and the prefix of them it saw
-//    land; before the CTA exits it waits (kDrainLimitNs each) for every load
-//    of the difference, load q on buffer q mod NST at phase parity
-//    (q / NST) mod 2, so no bulk copy still writes shared memory when the
-//    CTA's shared memory is released.
+//  - before the CTA exits, thread 0 works out from its cursor how many loads
+//    it issued, and from the step at which it gave up (if it did) the prefix
+//    of them it saw land; it waits (kDrainLimitNs each) for every load of the
+//    difference, load q on buffer q mod NST at phase parity (q / NST) mod 2,
+//    so no bulk copy still writes shared memory when the CTA's shared memory
+//    is released.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -62,6 +63,17 @@ struct FixedParams {
   uint32_t one;
   uint64_t wait_ns;  // limit of one barrier wait (0: a single non-blocking test)
 };
+
+// Thread 0, before the CTA exits: `issued` loads went out (load q into buffer
+// q mod nst, completing phase q / nst), and thread 0 saw loads 0 .. stop_g - 1
+// land (stop_g < 0: all of them).  Wait for each of the others; at most one
+// per buffer is outstanding and every earlier phase of its buffer completed,
+// so the parity names the phase unambiguously.
+__device__ __forceinline__ void drain_loads(uint64_t* full, int nst, int64_t issued,
+                                            int64_t stop_g) {
+  for (int64_t q = stop_g < 0 ? issued : stop_g; q < issued; ++q)
+    mbar_wait_bounded(&full[q % nst], static_cast<uint32_t>((q / nst) & 1), kDrainLimitNs);
+}
 
 // Give up on the pipeline: record the timeout and raise the CTA's flag, which
 // every thread still blocked in a wait then sees.
@@ -124,7 +136,7 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
   // Producer cursor (thread 0 only): the (tile, window) of the next load.
   int64_t p_tile = blockIdx.x, p_k = 0;
   int p_buf = 0;
-  int64_t issued = 0, confirmed = 0;  // loads issued / the prefix seen landed
+  int64_t stop_g = -1;  // thread 0: the step at which it gave up (-1: never)
   auto issue_next = [&]() {
     mbar_arrive_expect_tx(&full[p_buf], L::kStageBytes);
 #pragma unroll
@@ -139,7 +151,6 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
       p_tile += gridDim.x;
     }
     p_buf = (p_buf + 1 == NST) ? 0 : p_buf + 1;
-    ++issued;
   };
   if (t == 0)
     for (int64_t g = 0; g < NST && g < total; ++g) issue_next();
@@ -175,6 +186,7 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
         const int w = mbar_wait_or_flag(&full[b], parity, p.wait_ns, abort_flag);
         if (w != kWaitDone) {
           ok = false;
+          if (t == 0) stop_g = g;
           if (w == kWaitTimedOut) give_up(abort_flag, p.err);
         }
       }
@@ -205,8 +217,7 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
       __syncwarp();
       const bool live = __any_sync(kFullMask, ok);
       if (lane == 0 && live) mbar_arrive(&empty[b]);
-      if (t == 0 && ok) {
-        confirmed = g + 1;  // this thread saw load g land
+      if (t == 0 && ok) {  // this thread saw load g land
         if (g + NST < total) {
           // Refill this buffer once every warp has read it.
           const int w = mbar_wait_or_flag(&empty[b], parity, p.wait_ns, abort_flag);
@@ -245,8 +256,7 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
   // Loads issued but not seen landing (only after giving up) land before
   // the CTA exits.
   if (t == 0)
-    for (int64_t q = confirmed; q < issued; ++q)
-      mbar_wait_bounded(&full[q % NST], static_cast<uint32_t>((q / NST) & 1), kDrainLimitNs);
+    drain_loads(full, NST, (p_tile - blockIdx.x) / gridDim.x * steps + p_k, stop_g);
 }
 
 // Two threads per message, for batches too small to fill the GPU: threads
@@ -297,7 +307,7 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
 
   int64_t p_tile = blockIdx.x, p_k = 0;
   int p_buf = 0;
-  int64_t issued = 0, confirmed = 0;  // loads issued / the prefix seen landed
+  int64_t stop_g = -1;  // thread 0: the step at which it gave up (-1: never)
   auto issue_next = [&]() {
     mbar_arrive_expect_tx(&full[p_buf], L::kStageBytes);
 #pragma unroll
@@ -310,7 +320,6 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
       p_tile += gridDim.x;
     }
     p_buf = (p_buf + 1 == NST) ? 0 : p_buf + 1;
-    ++issued;
   };
   if (t == 0)
     for (int64_t g = 0; g < NST && g < total; ++g) issue_next();
@@ -342,6 +351,7 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
         const int w = mbar_wait_or_flag(&full[b], parity, p.wait_ns, abort_flag);
         if (w != kWaitDone) {
           ok = false;
+          if (t == 0) stop_g = g;
           if (w == kWaitTimedOut) give_up(abort_flag, p.err);
         }
       }
@@ -368,8 +378,7 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
       __syncwarp();
       const bool live = __any_sync(kFullMask, ok);
       if (lane == 0 && live) mbar_arrive(&empty[b]);
-      if (t == 0 && ok) {
-        confirmed = g + 1;  // this thread saw load g land
+      if (t == 0 && ok) {  // this thread saw load g land
         if (g + NST < total) {
           const int w = mbar_wait_or_flag(&empty[b], parity, p.wait_ns, abort_flag);
           if (w == kWaitDone) {
@@ -401,8 +410,7 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
     }
   }
   if (t == 0)
-    for (int64_t q = confirmed; q < issued; ++q)
-      mbar_wait_bounded(&full[q % NST], static_cast<uint32_t>((q / NST) & 1), kDrainLimitNs);
+    drain_loads(full, NST, (p_tile - blockIdx.x) / gridDim.x * steps + p_k, stop_g);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,

@@ -5,8 +5,10 @@
 builds one seeded batch on cuda:0 and hashes it `--reps` times through the C
 ABI (the first launch warms up; profile with `-s 1 -c 1` to capture the
 second).  Kinds: fixed (hh_hash_fixed), ragged (log-uniform lengths,
-per-message keys), short (0..64-byte messages) and long (n messages of
-`--length` bytes through the offsets form: solo or pair tiles from 128 KiB).
+per-message keys), short (0..64-byte messages), long (n messages of
+`--length` bytes through the offsets form: solo or pair tiles from 128 KiB)
+and siptree (n messages of `--length` bytes, SipTreeHash through
+hh_siptree_batch; --bits 13 for SipTreeHash13).
 """
 import argparse
 
@@ -17,7 +19,8 @@ from paper_1612_06257_gb300 import hh, workloads
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("--kind", choices=["fixed", "ragged", "short", "long"], default="fixed")
+    p.add_argument("--kind", choices=["fixed", "ragged", "short", "long", "siptree"],
+                   default="fixed")
     p.add_argument("--n", type=int, default=1 << 18)
     p.add_argument("--length", type=int, default=1024)
     p.add_argument("--bits", type=int, default=64)
@@ -31,13 +34,19 @@ def main():
         w = workloads.fixed(a.n, a.length, seed=1, device=dev)
     elif a.kind == "ragged":
         w = workloads.ragged(a.n, seed=1, device=dev)
-    elif a.kind == "long":
-        w = workloads.from_lengths([a.length] * a.n, seed=1, device=dev)
+    elif a.kind in ("long", "siptree"):
+        w = workloads.from_lengths([a.length] * a.n, seed=1, device=dev,
+                                   per_message_keys=a.kind == "long")
     else:
         w = workloads.short(a.n, seed=1, device=dev)
-    out = torch.empty(w.n * a.bits // 64, dtype=torch.int64, device=dev)
+    hh.hh_reserve(ctx, w.n)  # the length sort's scratch for this batch
+    words = 1 if a.kind == "siptree" else a.bits // 64
+    out = torch.empty(w.n * words, dtype=torch.int64, device=dev)
     for _ in range(a.reps):
-        if a.kind == "fixed":
+        if a.kind == "siptree":
+            variant = hh.HH_SIPTREE13 if a.bits == 13 else hh.HH_SIPTREE
+            hh.hh_siptree_batch(ctx, variant, w.keys, w.key_mode, w.data, w.offsets, out=out)
+        elif a.kind == "fixed":
             hh.hh_hash_fixed(ctx, a.bits, w.keys, w.key_mode, w.data, a.length, w.n, out=out)
         else:
             fn = {64: hh.hh_hash64_batch, 128: hh.hh_hash128_batch, 256: hh.hh_hash256_batch}

@@ -69,6 +69,29 @@ def test_results_alone_equal_results_in_the_mix(pool, use_graphs):
         assert np.array_equal(mixed.result[pick], expect), mixed.rid
 
 
+def test_file_sized_message_in_the_mix_matches_the_oracle(pool):
+    """A request carrying a 16 MiB + 5 B message at an unaligned start (one
+    warp or two threads per message on the device), served beside short and
+    1 KiB messages of other requests, checked against the oracle."""
+    big = serve.Request(key=np.array([1, 2, 3, 4], np.uint64),
+                        starts=np.array([3, 77, (1 << 20) + 1], np.int64),
+                        lengths=np.array([(16 << 20) + 5, 40, 1024], np.int64), rid=0)
+    others = _requests(12, count=6)
+    for r in others:
+        r.rid += 1
+    server = serve.HashServer(pool, bits=64, slots=2, capacity=4096, max_requests_per_batch=4,
+                              max_bytes_in_flight=64 << 20, use_graphs=True)
+    try:
+        serve.run_poisson(server, [big] + others, rate_per_s=5000.0, seed=4)
+        assert server.device_errors() == [0, 0]
+    finally:
+        server.close()
+    host_pool = pool.cpu().numpy()
+    expect = oracle_segments(big.key.view(np.int64).reshape(1, 4), np.zeros(3, np.int32),
+                             host_pool, big.starts, big.lengths, 64)
+    assert np.array_equal(big.result, expect)
+
+
 def test_requests_that_can_never_fit_are_rejected(pool):
     server = serve.HashServer(pool, slots=1, capacity=64, max_bytes_in_flight=1 << 20,
                               use_graphs=False)

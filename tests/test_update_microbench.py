@@ -1,9 +1,10 @@
 """GPU test: every Update-microbenchmark variant computes Section 4.2's Update.
 
 The kernels' output words are checked against the independent Python
-transcription (tests/ref_py/hh_ref.py), for the whole-state variants 0..5
-and the lane-pair variants 6..11, with the small launch (one block of 64
-threads) used to time a single Update chain.
+transcription (tests/ref_py/hh_ref.py), for the whole-state variants 0..5,
+the lane-pair variants 6..11 and the one-lane-per-thread variant 12, with
+the small launch (one block of 64 threads) used to time a single Update
+chain.
 """
 import numpy as np
 import pytest
@@ -62,10 +63,21 @@ def test_lane_pair_variants(ctx):
         assert out.cpu().numpy().view(np.uint64).tolist() == expect, v
 
 
+def test_quad_variant(ctx):
+    """One lane per thread, ZipperMerge partners exchanged by shuffle."""
+    expect = []
+    for s in range(THREADS // 4):
+        h = _state_after(_key(s), [4 * s, 4 * s + 1, 4 * s + 2, 4 * s + 3])
+        expect += h
+    out = hh.hh_update_microbench(ctx, 12, UPDATES, THREADS)
+    torch.cuda.synchronize()
+    assert out.cpu().numpy().view(np.uint64).tolist() == expect
+
+
 def test_thread_count_rules(ctx):
     out = torch.empty(512, dtype=torch.int64, device="cuda:0")
     for bad in (0, 16, 48 + 1, 288):
         with pytest.raises(hh.HHError):
             hh.hh_update_microbench(ctx, 1, 1, bad, out=out)
     with pytest.raises(hh.HHError):
-        hh.hh_update_microbench(ctx, 12, 1, 32, out=out)
+        hh.hh_update_microbench(ctx, 13, 1, 32, out=out)
