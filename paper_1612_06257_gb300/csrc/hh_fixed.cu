@@ -16,26 +16,25 @@
 // the end of a message and rows past the end of the batch are zero-filled by
 // the TMA unit; they are never hashed.
 //
-// Giving up (a barrier wait that runs past the context's limit) is
-// CTA-wide and keeps the barrier protocol intact:
-//  - the thread that gives up sets a shared flag; a thread whose wait is
-//    still blocked reads the flag (only in the blocked path) and gives up
-//    too.  A thread that gave up neither waits nor hashes, and writes zero
-//    hashes; a thread whose every wait succeeded hashed landed data.
-//  - a warp arrives on an "empty" barrier only while some lane of it is
-//    still live, so a warp whose lanes all gave up (and no longer wait) never
-//    races ahead into a later phase: every "empty" phase completes only when
-//    every warp has really finished reading that buffer, and a refill never
-//    overwrites data still being read.
+// Giving up (a barrier wait that runs past the context's limit) keeps the
+// barrier protocol intact, so no bulk copy is in flight when a CTA exits:
+//  - a thread whose wait runs out records the timeout and stops hashing (it
+//    writes zero hashes), but keeps waiting for that phase and every later
+//    one, each for at most kDrainLimitNs.  So every warp still arrives on
+//    every "empty" phase only after all its lanes are past that step: no
+//    warp races ahead into a later phase, every "empty" phase completes only
+//    when every warp has finished with its buffer, and a refill never
+//    overwrites data a thread still reads.  A thread whose every wait
+//    succeeded within the limit writes its exact hash.
 //  - thread 0 refills a buffer only after it has itself seen the buffer's
-//    previous load land, so at most one load per buffer is in flight and no
-//    "full" phase is armed twice.
-//  - before the CTA exits, thread 0 works out from its cursor how many loads
-//    it issued, and from the step at which it gave up (if it did) the prefix
-//    of them it saw land; it waits (kDrainLimitNs each) for every load of the
-//    difference, load q on buffer q mod NST at phase parity (q / NST) mod 2,
-//    so no bulk copy still writes shared memory when the CTA's shared memory
-//    is released.
+//    previous load land (and stops refilling if an "empty" wait fails), so
+//    at most one load per buffer is in flight and no "full" phase is armed
+//    twice.
+//  - only if a phase does not complete even within the drain limit (a copy
+//    that never lands) does a thread stop waiting altogether.  Before the
+//    CTA exits, thread 0 works out from its cursor how many loads it issued
+//    and waits (kDrainLimitNs each) for those it did not see land, load q on
+//    buffer q mod NST at phase parity (q / NST) mod 2.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -49,7 +48,6 @@ namespace hh {
 namespace {
 
 constexpr int kRows = 128;           // messages per tile = box height = threads
-constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kBoxBytes = 128 * kRows;
 
 struct FixedParams {
@@ -75,13 +73,6 @@ __device__ __forceinline__ void drain_loads(uint64_t* full, int nst, int64_t iss
     mbar_wait_bounded(&full[q % nst], static_cast<uint32_t>((q / nst) & 1), kDrainLimitNs);
 }
 
-// Give up on the pipeline: record the timeout and raise the CTA's flag, which
-// every thread still blocked in a wait then sees.
-__device__ __forceinline__ void give_up(volatile int* flag, int* err) {
-  *flag = 1;
-  __threadfence_block();
-  record_error(err, kErrTimeout);
-}
 
 template <int W, int NST, int M>
 struct FixedLayout {
@@ -120,8 +111,6 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = my_tiles * steps;                    // this CTA's (tile, window) stream
 
-  __shared__ int s_abort;
-  volatile int* abort_flag = &s_abort;
   if (t == 0) {
     prefetch_tensormap(&tmap);
     for (int i = 0; i < NST; ++i) {
@@ -129,14 +118,14 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
       mbar_init(&empty[i], kRows / 32);
     }
     fence_mbar_init();
-    s_abort = 0;
   }
   __syncthreads();
 
   // Producer cursor (thread 0 only): the (tile, window) of the next load.
   int64_t p_tile = blockIdx.x, p_k = 0;
   int p_buf = 0;
-  int64_t stop_g = -1;  // thread 0: the step at which it gave up (-1: never)
+  int64_t stop_g = -1;  // thread 0: the step from which it stopped waiting (-1: never)
+  bool stopped = false;  // thread 0: an "empty" wait failed, no further loads
   auto issue_next = [&]() {
     mbar_arrive_expect_tx(&full[p_buf], L::kStageBytes);
 #pragma unroll
@@ -165,7 +154,8 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
     for (int i = 0; i < 4; ++i) key[i] = __ldg(p.keys + i);
   }
   State s[M];
-  bool ok = true;
+  bool ok = true;       // every wait so far succeeded within the limit
+  bool broken = false;  // a phase did not complete within the drain limit
   int b = 0;                // stage buffer of the current window
   uint32_t parity = 0;      // its phase parity
   int64_t g = 0;            // position in this CTA's (tile, window) stream
@@ -182,13 +172,15 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
       init(s[i], key);
     }
     for (int64_t k = 0; k < steps; ++k, ++g) {
-      if (ok) {
-        const int w = mbar_wait_or_flag(&full[b], parity, p.wait_ns, abort_flag);
-        if (w != kWaitDone) {
+      if (!broken && !mbar_wait_bounded(&full[b], parity, ok ? p.wait_ns : kDrainLimitNs)) {
+        if (ok) {
+          record_error(p.err, kErrTimeout);
           ok = false;
-          if (t == 0) stop_g = g;
-          if (w == kWaitTimedOut) give_up(abort_flag, p.err);
+          broken = !mbar_wait_bounded(&full[b], parity, kDrainLimitNs);
+        } else {
+          broken = true;
         }
+        if (t == 0 && broken) stop_g = g;
       }
       const uint8_t* stage = smem + b * L::kStageBytes;
       if (ok) {
@@ -215,18 +207,16 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
         }
       }
       __syncwarp();
-      const bool live = __any_sync(kFullMask, ok);
-      if (lane == 0 && live) mbar_arrive(&empty[b]);
-      if (t == 0 && ok) {  // this thread saw load g land
-        if (g + NST < total) {
-          // Refill this buffer once every warp has read it.
-          const int w = mbar_wait_or_flag(&empty[b], parity, p.wait_ns, abort_flag);
-          if (w == kWaitDone) {
-            fence_proxy_async_smem();
-            issue_next();
-          } else if (w == kWaitTimedOut) {
-            give_up(abort_flag, p.err);
-          }
+      if (lane == 0) mbar_arrive(&empty[b]);
+      if (t == 0 && !broken && !stopped && g + NST < total) {
+        // Refill this buffer once every warp has read it (thread 0 saw its
+        // previous load land: it is not broken).
+        if (mbar_wait_bounded(&empty[b], parity, ok ? p.wait_ns : kDrainLimitNs)) {
+          fence_proxy_async_smem();
+          issue_next();
+        } else {
+          if (ok) record_error(p.err, kErrTimeout);
+          stopped = true;
         }
       }
       if (++b == NST) {
@@ -292,8 +282,6 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = my_tiles * steps;
 
-  __shared__ int s_abort;
-  volatile int* abort_flag = &s_abort;
   if (t == 0) {
     prefetch_tensormap(&tmap);
     for (int i = 0; i < NST; ++i) {
@@ -301,13 +289,13 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
       mbar_init(&empty[i], kWarps);
     }
     fence_mbar_init();
-    s_abort = 0;
   }
   __syncthreads();
 
   int64_t p_tile = blockIdx.x, p_k = 0;
   int p_buf = 0;
-  int64_t stop_g = -1;  // thread 0: the step at which it gave up (-1: never)
+  int64_t stop_g = -1;  // thread 0: the step from which it stopped waiting (-1: never)
+  bool stopped = false;  // thread 0: an "empty" wait failed, no further loads
   auto issue_next = [&]() {
     mbar_arrive_expect_tx(&full[p_buf], L::kStageBytes);
 #pragma unroll
@@ -334,7 +322,8 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
     for (int i = 0; i < 4; ++i) key[i] = __ldg(p.keys + i);
   }
   Half s;
-  bool ok = true;
+  bool ok = true;       // every wait so far succeeded within the limit
+  bool broken = false;  // a phase did not complete within the drain limit
   int b = 0;
   uint32_t parity = 0;
   int64_t g = 0;
@@ -347,13 +336,15 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
     }
     init_half(s, key, half);
     for (int64_t k = 0; k < steps; ++k, ++g) {
-      if (ok) {
-        const int w = mbar_wait_or_flag(&full[b], parity, p.wait_ns, abort_flag);
-        if (w != kWaitDone) {
+      if (!broken && !mbar_wait_bounded(&full[b], parity, ok ? p.wait_ns : kDrainLimitNs)) {
+        if (ok) {
+          record_error(p.err, kErrTimeout);
           ok = false;
-          if (t == 0) stop_g = g;
-          if (w == kWaitTimedOut) give_up(abort_flag, p.err);
+          broken = !mbar_wait_bounded(&full[b], parity, kDrainLimitNs);
+        } else {
+          broken = true;
         }
+        if (t == 0 && broken) stop_g = g;
       }
       const uint8_t* stage = smem + b * L::kStageBytes;
       if (ok) {
@@ -376,17 +367,14 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
         }
       }
       __syncwarp();
-      const bool live = __any_sync(kFullMask, ok);
-      if (lane == 0 && live) mbar_arrive(&empty[b]);
-      if (t == 0 && ok) {  // this thread saw load g land
-        if (g + NST < total) {
-          const int w = mbar_wait_or_flag(&empty[b], parity, p.wait_ns, abort_flag);
-          if (w == kWaitDone) {
-            fence_proxy_async_smem();
-            issue_next();
-          } else if (w == kWaitTimedOut) {
-            give_up(abort_flag, p.err);
-          }
+      if (lane == 0) mbar_arrive(&empty[b]);
+      if (t == 0 && !broken && !stopped && g + NST < total) {
+        if (mbar_wait_bounded(&empty[b], parity, ok ? p.wait_ns : kDrainLimitNs)) {
+          fence_proxy_async_smem();
+          issue_next();
+        } else {
+          if (ok) record_error(p.err, kErrTimeout);
+          stopped = true;
         }
       }
       if (++b == NST) {

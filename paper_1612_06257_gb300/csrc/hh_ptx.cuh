@@ -101,28 +101,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
-// Wait for a phase of an mbarrier as mbar_wait_bounded does, but also stop
-// (returning kWaitAbandoned) once *flag is non-zero.  The flag is read only
-// in a wait that has already lasted kFlagAfterNs, far longer than any
-// pipeline wait that makes progress, so ordinary waits never touch it.
-// Returns kWaitDone, kWaitAbandoned or kWaitTimedOut (limit 0: one
-// non-blocking test, done or timed out).
-constexpr int kWaitDone = 0, kWaitAbandoned = 1, kWaitTimedOut = 2;
-constexpr uint64_t kFlagAfterNs = 20000;  // 20 us
-__device__ __forceinline__ int mbar_wait_or_flag(uint64_t* bar, uint32_t parity,
-                                                 uint64_t limit_ns, volatile int* flag) {
-  const uint32_t a = smem_u32(bar);
-  if (limit_ns == 0) return mbar_test_wait(a, parity) ? kWaitDone : kWaitTimedOut;
-  if (mbar_try_wait(a, parity)) return kWaitDone;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(a, parity)) {
-    const uint64_t waited = global_ns() - t0;
-    if (waited > limit_ns) return kWaitTimedOut;
-    if (waited > kFlagAfterNs && *flag != 0) return kWaitAbandoned;
-  }
-  return kWaitDone;
-}
-
 // 128-bit shared-memory load (kept as one LDS.128; the address must be
 // 16-byte aligned).
 __device__ __forceinline__ uint4 lds128(const void* p) {
