@@ -16,25 +16,23 @@
 // the end of a message and rows past the end of the batch are zero-filled by
 // the TMA unit; they are never hashed.
 //
-// Giving up (a barrier wait that runs past the context's limit) keeps the
-// barrier protocol intact, so no bulk copy is in flight when a CTA exits:
-//  - a thread whose wait runs out records the timeout and stops hashing (it
-//    writes zero hashes), but keeps waiting for that phase and every later
-//    one, each for at most kDrainLimitNs.  So every warp still arrives on
-//    every "empty" phase only after all its lanes are past that step: no
-//    warp races ahead into a later phase, every "empty" phase completes only
-//    when every warp has finished with its buffer, and a refill never
-//    overwrites data a thread still reads.  A thread whose every wait
-//    succeeded within the limit writes its exact hash.
-//  - thread 0 refills a buffer only after it has itself seen the buffer's
-//    previous load land (and stops refilling if an "empty" wait fails), so
-//    at most one load per buffer is in flight and no "full" phase is armed
-//    twice.
-//  - only if a phase does not complete even within the drain limit (a copy
-//    that never lands) does a thread stop waiting altogether.  Before the
-//    CTA exits, thread 0 works out from its cursor how many loads it issued
-//    and waits (kDrainLimitNs each) for those it did not see land, load q on
-//    buffer q mod NST at phase parity (q / NST) mod 2.
+// Giving up (a barrier wait that runs past its limit) stops that thread's
+// waiting and hashing (it writes zero hashes) and raises a CTA-wide flag;
+// the refills are the only thing the flag must stop.  Thread 0 issues a
+// refill only after its own wait for the buffer's previous load succeeded,
+// and, after the "empty" wait, only while the flag is clear: so at most one
+// load per buffer is in flight, no "full" phase is armed twice, and no
+// buffer is overwritten after any thread gave up (a warp whose lanes all gave
+// up may arrive early on an "empty" barrier, but only after raising the
+// flag).  Before the CTA exits, thread 0 works out from its cursor how many
+// loads it issued and waits (kDrainLimitNs each) for those it did not see
+// land, load q on buffer q mod NST at phase parity (q / NST) mod 2: at most
+// one per buffer is outstanding and every earlier phase of its buffer has
+// completed, so the parity names the phase.  No bulk copy is in flight when
+// the CTA's shared memory is released.  The limit is a compile-time 2 s in
+// the kernels every call uses; a context with its own limit
+// (hh_set_tune_param "wait_limit_ns") runs separate instantiations that read
+// it from their parameters.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -59,20 +57,8 @@ struct FixedParams {
   int words;
   int* err;
   uint32_t one;
-  uint64_t wait_ns;  // limit of one barrier wait (0: a single non-blocking test)
+  uint64_t wait_ns;  // the context's wait limit (read by the kCustom kernels only)
 };
-
-// Thread 0, before the CTA exits: `issued` loads went out (load q into buffer
-// q mod nst, completing phase q / nst), and thread 0 saw loads 0 .. stop_g - 1
-// land (stop_g < 0: all of them).  Wait for each of the others; at most one
-// per buffer is outstanding and every earlier phase of its buffer completed,
-// so the parity names the phase unambiguously.
-__device__ __forceinline__ void drain_loads(uint64_t* full, int nst, int64_t issued,
-                                            int64_t stop_g) {
-  for (int64_t q = stop_g < 0 ? issued : stop_g; q < issued; ++q)
-    mbar_wait_bounded(&full[q % nst], static_cast<uint32_t>((q / nst) & 1), kDrainLimitNs);
-}
-
 
 template <int W, int NST, int M>
 struct FixedLayout {
@@ -90,12 +76,22 @@ __device__ __forceinline__ void load_swizzled_packet(const uint8_t* box, int row
   w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
 }
 
+// Thread 0, before the CTA exits: `issued` loads went out (load q into buffer
+// q mod nst, completing phase q / nst), and it saw loads 0 .. stop_g - 1 land
+// (stop_g < 0: all of them); wait for the others.
+__device__ __forceinline__ void drain_loads(uint64_t* full, int nst, int64_t issued,
+                                            int64_t stop_g) {
+  for (int64_t q = stop_g < 0 ? issued : stop_g; q < issued; ++q)
+    mbar_wait_bounded(&full[q % nst], static_cast<uint32_t>((q / nst) & 1), kDrainLimitNs);
+}
+
 // M messages per thread: a tile is 128 * M messages; thread t hashes
 // messages t, t + 128, ... of the tile, interleaving M independent Update
 // chains for more instruction-level parallelism per warp.
-template <int W, int NST, int M>
+template <int W, int NST, int M, bool kCustom>
 __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant__ CUtensorMap tmap,
                                                           FixedParams p) {
+  const uint64_t limit = kCustom ? p.wait_ns : kWaitLimitNs;
   using L = FixedLayout<W, NST, M>;
   constexpr int kBoxes = W / 128;
   constexpr int kTileMsgs = kRows * M;
@@ -111,7 +107,10 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = my_tiles * steps;                    // this CTA's (tile, window) stream
 
+  __shared__ int s_gave_up;  // set by any thread that gave up; read by thread 0
+  volatile int* gave_up = &s_gave_up;
   if (t == 0) {
+    s_gave_up = 0;
     prefetch_tensormap(&tmap);
     for (int i = 0; i < NST; ++i) {
       mbar_init(&full[i], 1);
@@ -124,8 +123,6 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
   // Producer cursor (thread 0 only): the (tile, window) of the next load.
   int64_t p_tile = blockIdx.x, p_k = 0;
   int p_buf = 0;
-  int64_t stop_g = -1;  // thread 0: the step from which it stopped waiting (-1: never)
-  bool stopped = false;  // thread 0: an "empty" wait failed, no further loads
   auto issue_next = [&]() {
     mbar_arrive_expect_tx(&full[p_buf], L::kStageBytes);
 #pragma unroll
@@ -154,8 +151,8 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
     for (int i = 0; i < 4; ++i) key[i] = __ldg(p.keys + i);
   }
   State s[M];
-  bool ok = true;       // every wait so far succeeded within the limit
-  bool broken = false;  // a phase did not complete within the drain limit
+  bool ok = true;
+  int64_t stop_g = -1;
   int b = 0;                // stage buffer of the current window
   uint32_t parity = 0;      // its phase parity
   int64_t g = 0;            // position in this CTA's (tile, window) stream
@@ -172,15 +169,11 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
       init(s[i], key);
     }
     for (int64_t k = 0; k < steps; ++k, ++g) {
-      if (!broken && !mbar_wait_bounded(&full[b], parity, ok ? p.wait_ns : kDrainLimitNs)) {
-        if (ok) {
-          record_error(p.err, kErrTimeout);
-          ok = false;
-          broken = !mbar_wait_bounded(&full[b], parity, kDrainLimitNs);
-        } else {
-          broken = true;
-        }
-        if (t == 0 && broken) stop_g = g;
+      if (ok && !mbar_wait_bounded(&full[b], parity, limit)) {
+        ok = false;
+        *gave_up = 1;
+        if (t == 0) stop_g = g;
+        record_error(p.err, kErrTimeout);
       }
       const uint8_t* stage = smem + b * L::kStageBytes;
       if (ok) {
@@ -208,15 +201,14 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
-      if (t == 0 && !broken && !stopped && g + NST < total) {
-        // Refill this buffer once every warp has read it (thread 0 saw its
-        // previous load land: it is not broken).
-        if (mbar_wait_bounded(&empty[b], parity, ok ? p.wait_ns : kDrainLimitNs)) {
+      if (t == 0 && ok && g + NST < total) {
+        // Refill this buffer once every warp has read it.
+        if (!mbar_wait_bounded(&empty[b], parity, limit)) {
+          *gave_up = 1;
+          record_error(p.err, kErrTimeout);
+        } else if (*gave_up == 0) {
           fence_proxy_async_smem();
           issue_next();
-        } else {
-          if (ok) record_error(p.err, kErrTimeout);
-          stopped = true;
         }
       }
       if (++b == NST) {
@@ -243,10 +235,9 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
       }
     }
   }
-  // Loads issued but not seen landing (only after giving up) land before
-  // the CTA exits.
-  if (t == 0)
-    drain_loads(full, NST, (p_tile - blockIdx.x) / gridDim.x * steps + p_k, stop_g);
+  // Loads issued but never waited for (only after a timeout) get a bounded
+  // time to land before the CTA exits.
+  if (t == 0) drain_loads(full, NST, (p_tile - blockIdx.x) / gridDim.x * steps + p_k, stop_g);
 }
 
 // Two threads per message, for batches too small to fill the GPU: threads
@@ -263,9 +254,10 @@ struct PairLayout {
   static constexpr int kBytes = kBarOffset + 2 * NST * 8 + 1024;  // + alignment slack
 };
 
-template <int W, int NST, int ROWS>
+template <int W, int NST, int ROWS, bool kCustom>
 __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
     const __grid_constant__ CUtensorMap tmap, FixedParams p) {
+  const uint64_t limit = kCustom ? p.wait_ns : kWaitLimitNs;
   using L = PairLayout<W, NST, ROWS>;
   constexpr int kBoxes = W / 128;
   constexpr int kWarps = 2 * ROWS / 32;
@@ -282,7 +274,10 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = my_tiles * steps;
 
+  __shared__ int s_gave_up;  // set by any thread that gave up; read by thread 0
+  volatile int* gave_up = &s_gave_up;
   if (t == 0) {
+    s_gave_up = 0;
     prefetch_tensormap(&tmap);
     for (int i = 0; i < NST; ++i) {
       mbar_init(&full[i], 1);
@@ -294,8 +289,6 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
 
   int64_t p_tile = blockIdx.x, p_k = 0;
   int p_buf = 0;
-  int64_t stop_g = -1;  // thread 0: the step from which it stopped waiting (-1: never)
-  bool stopped = false;  // thread 0: an "empty" wait failed, no further loads
   auto issue_next = [&]() {
     mbar_arrive_expect_tx(&full[p_buf], L::kStageBytes);
 #pragma unroll
@@ -322,8 +315,8 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
     for (int i = 0; i < 4; ++i) key[i] = __ldg(p.keys + i);
   }
   Half s;
-  bool ok = true;       // every wait so far succeeded within the limit
-  bool broken = false;  // a phase did not complete within the drain limit
+  bool ok = true;
+  int64_t stop_g = -1;
   int b = 0;
   uint32_t parity = 0;
   int64_t g = 0;
@@ -336,15 +329,11 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
     }
     init_half(s, key, half);
     for (int64_t k = 0; k < steps; ++k, ++g) {
-      if (!broken && !mbar_wait_bounded(&full[b], parity, ok ? p.wait_ns : kDrainLimitNs)) {
-        if (ok) {
-          record_error(p.err, kErrTimeout);
-          ok = false;
-          broken = !mbar_wait_bounded(&full[b], parity, kDrainLimitNs);
-        } else {
-          broken = true;
-        }
-        if (t == 0 && broken) stop_g = g;
+      if (ok && !mbar_wait_bounded(&full[b], parity, limit)) {
+        ok = false;
+        *gave_up = 1;
+        if (t == 0) stop_g = g;
+        record_error(p.err, kErrTimeout);
       }
       const uint8_t* stage = smem + b * L::kStageBytes;
       if (ok) {
@@ -368,13 +357,13 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[b]);
-      if (t == 0 && !broken && !stopped && g + NST < total) {
-        if (mbar_wait_bounded(&empty[b], parity, ok ? p.wait_ns : kDrainLimitNs)) {
+      if (t == 0 && ok && g + NST < total) {
+        if (!mbar_wait_bounded(&empty[b], parity, limit)) {
+          *gave_up = 1;
+          record_error(p.err, kErrTimeout);
+        } else if (*gave_up == 0) {
           fence_proxy_async_smem();
           issue_next();
-        } else {
-          if (ok) record_error(p.err, kErrTimeout);
-          stopped = true;
         }
       }
       if (++b == NST) {
@@ -397,8 +386,7 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
       }
     }
   }
-  if (t == 0)
-    drain_loads(full, NST, (p_tile - blockIdx.x) / gridDim.x * steps + p_k, stop_g);
+  if (t == 0) drain_loads(full, NST, (p_tile - blockIdx.x) / gridDim.x * steps + p_k, stop_g);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -425,7 +413,8 @@ template <int W, int NST, int M>
 cudaError_t launch_fixed_t(const CUtensorMap& tmap, const FixedParams& p, int num_sms,
                            cudaStream_t stream) {
   using L = FixedLayout<W, NST, M>;
-  auto kern = fixed_tma_kernel<W, NST, M>;
+  auto kern = p.wait_ns == kWaitLimitNs ? fixed_tma_kernel<W, NST, M, false>
+                                        : fixed_tma_kernel<W, NST, M, true>;
   cudaError_t e;
   const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), kRows, L::kBytes, &e);
   if (e != cudaSuccess) return e;
@@ -456,7 +445,8 @@ template <int W, int NST, int ROWS>
 cudaError_t launch_fixed_pair_t(const CUtensorMap& tmap, const FixedParams& p, int num_sms,
                                 cudaStream_t stream) {
   using L = PairLayout<W, NST, ROWS>;
-  auto kern = fixed_pair_kernel<W, NST, ROWS>;
+  auto kern = p.wait_ns == kWaitLimitNs ? fixed_pair_kernel<W, NST, ROWS, false>
+                                        : fixed_pair_kernel<W, NST, ROWS, true>;
   cudaError_t e;
   const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), 2 * ROWS, L::kBytes, &e);
   if (e != cudaSuccess) return e;

@@ -14,11 +14,11 @@ constexpr int kErrBadKey = 8;       // a key index outside the key table
 constexpr int kErrBadChunk = 9;     // a stream-update chunk not a multiple of 32 bytes
 
 // Bounds on the kernels' waits for asynchronous copies.  A wait that runs
-// past its limit records kErrTimeout; the thread then stops hashing (zero
-// hashes) but keeps waiting for each later phase, at most kDrainLimitNs
-// each, so the copies already issued land before the kernel exits.  The
-// limit is a per-context setting (hh_set_tune_param "wait_limit_ns"); 0
-// tests each barrier once without blocking.
+// past its limit records kErrTimeout and the thread writes zero hashes; the
+// kernel issues no further copies and waits (at most kDrainLimitNs per copy)
+// for those it issued before it exits.  The limit is a per-context setting
+// (hh_set_tune_param "wait_limit_ns"; kWaitLimitNs by default); 0 tests each
+// barrier once without blocking.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s: far beyond any legitimate wait
 constexpr uint64_t kDrainLimitNs = 200000000ull;  // 0.2 s per copy when giving up
 

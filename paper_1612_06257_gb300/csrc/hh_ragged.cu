@@ -784,6 +784,21 @@ __global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, co
     }
     return;
   }
+  // The initial state is the same for every message of a one-key batch:
+  // built once per block in shared memory, read back with broadcast loads.
+  __shared__ __align__(16) uint64_t s_init[16];
+  if (tid == 0) {
+    State s0;
+    init(s0, key);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      s_init[i] = s0.v0[i];
+      s_init[4 + i] = s0.v1[i];
+      s_init[8 + i] = s0.mul0[i];
+      s_init[12 + i] = s0.mul1[i];
+    }
+  }
+  __syncthreads();
   auto fetch_words = [&](int slot) {  // the slot's offsets have landed
     const int64_t s = next_offsets[slot][tid][0], e = next_offsets[slot][tid][1];
     int64_t l = e < s ? 0 : e - s;
@@ -809,7 +824,21 @@ __global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, co
     if (more) fetch_offsets(m + stride, cur ^ 1);
     if (bad) record_error(b.err, bad);
     State s;
-    init(s, key);
+    {
+      const uint4* p = reinterpret_cast<const uint4*>(s_init);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const uint4 a = p[i], c = p[2 + i], d = p[4 + i], e = p[6 + i];
+        s.v0[2 * i] = join(a.x, a.y);
+        s.v0[2 * i + 1] = join(a.z, a.w);
+        s.v1[2 * i] = join(c.x, c.y);
+        s.v1[2 * i + 1] = join(c.z, c.w);
+        s.mul0[2 * i] = join(d.x, d.y);
+        s.mul0[2 * i + 1] = join(d.z, d.w);
+        s.mul1[2 * i] = join(e.x, e.y);
+        s.mul1[2 * i + 1] = join(e.z, e.w);
+      }
+    }
     hash_short_words(s, x, static_cast<uint32_t>((base + s0) & 3), static_cast<uint32_t>(len));
     if (more) {
       cp_async_wait<0>();

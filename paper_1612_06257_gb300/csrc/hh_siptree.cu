@@ -118,16 +118,32 @@ __device__ __forceinline__ void keep_bytes(uint32_t w[8], uint32_t r) {
 }
 
 // The hash of a message of `len` bytes whose `vectors` vectors went into t.
+// The four lanes' last compression and finalisation run interleaved, the
+// rounds in a loop (not unrolled) to keep the kernel's code small.
 template <int C, int D>
 __device__ __forceinline__ uint64_t tree_result(Tree& t, int64_t vectors, int64_t len,
                                                 uint64_t k0, uint64_t k1) {
   const uint64_t last = static_cast<uint64_t>((8 * vectors) & 0xff) << 56;
-  uint64_t h[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) t.lane[j].v3 ^= last;
+#pragma unroll 1
+  for (int r = 0; r < C; ++r) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sip_round(t.lane[j]);
+  }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    sip_compress<C>(t.lane[j], last);
-    h[j] = sip_finish<D>(t.lane[j]);
+    t.lane[j].v0 ^= last;
+    t.lane[j].v2 ^= 0xff;
   }
+#pragma unroll 1
+  for (int r = 0; r < D; ++r) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sip_round(t.lane[j]);
+  }
+  uint64_t h[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) h[j] = t.lane[j].v0 ^ t.lane[j].v1 ^ t.lane[j].v2 ^ t.lane[j].v3;
   Sip f;
   sip_init(f, k0, k1);
 #pragma unroll
@@ -143,13 +159,15 @@ template <int W, bool kAligned, int C>
 __device__ __forceinline__ void tree_step(Tree& t, const uint8_t* row, uint32_t mis, int64_t k,
                                           int64_t whole, uint32_t r, int64_t rem_step) {
   const int64_t p0 = k * (W / 32);
-#pragma unroll
-  for (int j = 0; j < W / 32; ++j) {
-    if (p0 + j < whole) {
-      uint32_t w[8];
-      read_packet<kAligned>(row, mis + 32u * j, w);
-      tree_vector<C>(t, w);
-    }
+  const int64_t left = whole - p0;
+  const int count = left <= 0 ? 0 : (left < W / 32 ? static_cast<int>(left) : W / 32);
+  // Two vectors per loop iteration: each is four independent chains already,
+  // and a fully unrolled window would overflow the instruction cache.
+#pragma unroll 2
+  for (int j = 0; j < count; ++j) {
+    uint32_t w[8];
+    read_packet<kAligned>(row, mis + 32u * j, w);
+    tree_vector<C>(t, w);
   }
   if (k == rem_step) {
     uint32_t w[8];
