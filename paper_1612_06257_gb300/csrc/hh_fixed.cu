@@ -17,22 +17,28 @@
 // the TMA unit; they are never hashed.
 //
 // Giving up (a barrier wait that runs past its limit) stops that thread's
-// waiting and hashing (it writes zero hashes) and raises a CTA-wide flag;
-// the refills are the only thing the flag must stop.  Thread 0 issues a
-// refill only after its own wait for the buffer's previous load succeeded,
-// and, after the "empty" wait, only while the flag is clear: so at most one
-// load per buffer is in flight, no "full" phase is armed twice, and no
-// buffer is overwritten after any thread gave up (a warp whose lanes all gave
-// up may arrive early on an "empty" barrier, but only after raising the
-// flag).  Before the CTA exits, thread 0 works out from its cursor how many
-// loads it issued and waits (kDrainLimitNs each) for those it did not see
-// land, load q on buffer q mod NST at phase parity (q / NST) mod 2: at most
-// one per buffer is outstanding and every earlier phase of its buffer has
-// completed, so the parity names the phase.  No bulk copy is in flight when
-// the CTA's shared memory is released.  The limit is a compile-time 2 s in
-// the kernels every call uses; a context with its own limit
-// (hh_set_tune_param "wait_limit_ns") runs separate instantiations that read
-// it from their parameters.
+// waiting and hashing (it writes zero hashes).  Three rules keep the
+// pipeline sound afterwards:
+//  - a warp arrives on an "empty" barrier only while its lane 0 is still
+//    live.  The lanes of a warp meet at __syncwarp every step, so a warp can
+//    run ahead of the real phases only once lane 0 has stopped waiting, and
+//    from then on it no longer arrives: every arrival means that warp has
+//    finished reading the buffer, and a refill never overwrites data in use
+//    (a warp that stops arriving makes the producer's next "empty" wait run
+//    out, which ends the refills);
+//  - thread 0 refills a buffer only after its own wait for the buffer's
+//    previous load succeeded, so at most one load per buffer is in flight
+//    and no "full" phase is armed twice; after an "empty" wait that ran out
+//    it issues nothing more;
+//  - before the CTA exits, thread 0 works out from its cursor how many loads
+//    it issued and waits (kDrainLimitNs each) for those it did not see land,
+//    load q on buffer q mod NST at phase parity (q / NST) mod 2: at most one
+//    per buffer is outstanding and every earlier phase of its buffer has
+//    completed, so the parity names the phase.  No bulk copy is in flight
+//    when the CTA's shared memory is released.
+// The limit is a compile-time 2 s in the kernels every call uses; a context
+// with its own limit (hh_set_tune_param "wait_limit_ns") runs separate
+// instantiations that read it from their parameters.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -107,10 +113,7 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = my_tiles * steps;                    // this CTA's (tile, window) stream
 
-  __shared__ int s_gave_up;  // set by any thread that gave up; read by thread 0
-  volatile int* gave_up = &s_gave_up;
   if (t == 0) {
-    s_gave_up = 0;
     prefetch_tensormap(&tmap);
     for (int i = 0; i < NST; ++i) {
       mbar_init(&full[i], 1);
@@ -152,7 +155,8 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
   }
   State s[M];
   bool ok = true;
-  int64_t stop_g = -1;
+  int64_t stop_g = -1;   // thread 0: the step at which it gave up (-1: never)
+  bool stopped = false;  // thread 0: an "empty" wait ran out; no further loads
   int b = 0;                // stage buffer of the current window
   uint32_t parity = 0;      // its phase parity
   int64_t g = 0;            // position in this CTA's (tile, window) stream
@@ -171,7 +175,6 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
     for (int64_t k = 0; k < steps; ++k, ++g) {
       if (ok && !mbar_wait_bounded(&full[b], parity, limit)) {
         ok = false;
-        *gave_up = 1;
         if (t == 0) stop_g = g;
         record_error(p.err, kErrTimeout);
       }
@@ -200,13 +203,13 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[b]);
-      if (t == 0 && ok && g + NST < total) {
+      if (lane == 0 && ok) mbar_arrive(&empty[b]);
+      if (t == 0 && ok && !stopped && g + NST < total) {
         // Refill this buffer once every warp has read it.
         if (!mbar_wait_bounded(&empty[b], parity, limit)) {
-          *gave_up = 1;
           record_error(p.err, kErrTimeout);
-        } else if (*gave_up == 0) {
+          stopped = true;  // refills stop for good: the cursor must stay in step
+        } else {
           fence_proxy_async_smem();
           issue_next();
         }
@@ -274,10 +277,7 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = my_tiles * steps;
 
-  __shared__ int s_gave_up;  // set by any thread that gave up; read by thread 0
-  volatile int* gave_up = &s_gave_up;
   if (t == 0) {
-    s_gave_up = 0;
     prefetch_tensormap(&tmap);
     for (int i = 0; i < NST; ++i) {
       mbar_init(&full[i], 1);
@@ -316,7 +316,8 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
   }
   Half s;
   bool ok = true;
-  int64_t stop_g = -1;
+  int64_t stop_g = -1;   // thread 0: the step at which it gave up (-1: never)
+  bool stopped = false;  // thread 0: an "empty" wait ran out; no further loads
   int b = 0;
   uint32_t parity = 0;
   int64_t g = 0;
@@ -331,7 +332,6 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
     for (int64_t k = 0; k < steps; ++k, ++g) {
       if (ok && !mbar_wait_bounded(&full[b], parity, limit)) {
         ok = false;
-        *gave_up = 1;
         if (t == 0) stop_g = g;
         record_error(p.err, kErrTimeout);
       }
@@ -356,12 +356,12 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[b]);
-      if (t == 0 && ok && g + NST < total) {
+      if (lane == 0 && ok) mbar_arrive(&empty[b]);
+      if (t == 0 && ok && !stopped && g + NST < total) {
         if (!mbar_wait_bounded(&empty[b], parity, limit)) {
-          *gave_up = 1;
           record_error(p.err, kErrTimeout);
-        } else if (*gave_up == 0) {
+          stopped = true;  // refills stop for good: the cursor must stay in step
+        } else {
           fence_proxy_async_smem();
           issue_next();
         }
