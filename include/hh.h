@@ -257,9 +257,8 @@ enum hh_regime {
  * only; 1 elsewhere) `messages_per_thread` interleaved messages per thread.
  * Supported (window, stages, messages_per_thread): HH_REGIME_FIXED
  * (128, 2..4, 1), (256, 2..3, 1), (128, 2..3, 2); HH_REGIME_RAGGED
- * (128, 2..4, 1), (256, 2..3, 1), (128, 2, 2) (two messages per lane:
- * warp tiles of 64); HH_REGIME_BULK (128, 3..4, 1), (256, 2..3, 1).  Others
- * return HH_ERR_INVALID_ARG. */
+ * (128, 2..4, 1), (256, 2..3, 1); HH_REGIME_BULK (128, 3..4, 1),
+ * (256, 2..3, 1).  Others return HH_ERR_INVALID_ARG. */
 int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages,
                         int messages_per_thread);
 

@@ -617,7 +617,7 @@ int hh_set_staged_shape(hh_ctx* ctx, int regime, int window, int stages,
                         int messages_per_thread) {
   if (ctx == nullptr || regime < HH_REGIME_FIXED || regime > HH_REGIME_BULK)
     return HH_ERR_INVALID_ARG;
-  if (regime == HH_REGIME_BULK && messages_per_thread != 1) return HH_ERR_INVALID_ARG;
+  if (regime != HH_REGIME_FIXED && messages_per_thread != 1) return HH_ERR_INVALID_ARG;
   const hh::StagedShape shape{window, stages, messages_per_thread};
   if (regime == HH_REGIME_FIXED) {
     if (!hh::fixed_shape_valid(shape)) return HH_ERR_INVALID_ARG;

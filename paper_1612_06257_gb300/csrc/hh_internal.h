@@ -114,10 +114,9 @@ cudaError_t launch_staged(const Batch& b, const Queue& q, StagedShape shape, boo
 int staged_blocks_per_sm(StagedShape shape, bool aligned16);
 size_t staged_smem_bytes(StagedShape shape);
 
-// Ragged batches: warp tiles of 32 M messages (M per lane), coalesced
-// cp.async staging.  Supported (window, stages, M):
-#define HH_RAGGED_SHAPES(X) \
-  X(128, 2, 1) X(128, 3, 1) X(128, 4, 1) X(256, 2, 1) X(256, 3, 1) X(128, 2, 2)
+// Ragged batches: warp tiles of 32 messages, coalesced cp.async staging.
+// Supported (window, stages) pairs:
+#define HH_RAGGED_SHAPES(X) X(128, 2) X(128, 3) X(128, 4) X(256, 2) X(256, 3)
 bool ragged_shape_valid(StagedShape shape);
 cudaError_t launch_ragged(const Batch& b, const Queue& q, StagedShape shape, int num_sms,
                           cudaStream_t stream);

@@ -76,49 +76,6 @@ __device__ __forceinline__ void hash_step(State& s, const uint8_t* row, uint32_t
   }
 }
 
-// Two messages per lane, both with a full window at this step (a full window
-// never holds the remainder packet): their Update chains are independent, so
-// they run interleaved for twice the instruction-level parallelism.
-template <int W, bool kAligned>
-__device__ __forceinline__ void hash_full2(State& sa, const uint8_t* ra, uint32_t ma, State& sb,
-                                           const uint8_t* rb, uint32_t mb) {
-  if (kAligned) {
-#pragma unroll
-    for (int j = 0; j < W / 32; ++j) {
-      uint32_t wa[8], wb[8];
-      read_packet<true>(ra, 32u * j, wa);
-      read_packet<true>(rb, 32u * j, wb);
-      update_words_v<kFastUpdate>(sa, wa, 1u);
-      update_words_v<kFastUpdate>(sb, wb, 1u);
-    }
-  } else {
-    const uint32_t* pa = reinterpret_cast<const uint32_t*>(ra + (ma & ~3u));
-    const uint32_t* pb = reinterpret_cast<const uint32_t*>(rb + (mb & ~3u));
-    const uint32_t sela = 0x3210u + 0x1111u * (ma & 3u), selb = 0x3210u + 0x1111u * (mb & 3u);
-    uint32_t preva = pa[0], prevb = pb[0];
-#pragma unroll
-    for (int j = 0; j < W / 32; ++j) {
-      uint32_t xa[8], xb[8], wa[8], wb[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        xa[i] = pa[8 * j + 1 + i];
-        xb[i] = pb[8 * j + 1 + i];
-      }
-      wa[0] = __byte_perm(preva, xa[0], sela);
-      wb[0] = __byte_perm(prevb, xb[0], selb);
-#pragma unroll
-      for (int i = 1; i < 8; ++i) {
-        wa[i] = __byte_perm(xa[i - 1], xa[i], sela);
-        wb[i] = __byte_perm(xb[i - 1], xb[i], selb);
-      }
-      preva = xa[7];
-      prevb = xb[7];
-      update_words_v<kFastUpdate>(sa, wa, 1u);
-      update_words_v<kFastUpdate>(sb, wb, 1u);
-    }
-  }
-}
-
 // Messages of at most 64 bytes (a whole warp of them), read straight from
 // global memory (load_short_words): at most 17 aligned 32-bit words per
 // message, shifted into place with one PRMT per word.  A message has at most
@@ -509,9 +466,9 @@ __device__ __forceinline__ void solo_tile(const Batch& b, const int32_t* perm, i
   __syncwarp();
 }
 
-template <int W, int NST, int WARPS, int M>
-__global__ void __launch_bounds__(WARPS * 32, M == 2 ? 3 : 2) ragged_kernel(Batch b, Queue q) {
-  using L = RaggedLayout<W, NST, M>;
+template <int W, int NST, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q) {
+  using L = RaggedLayout<W, NST>;
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* ring = smem + warp * L::kWarpBytes;
@@ -529,7 +486,7 @@ __global__ void __launch_bounds__(WARPS * 32, M == 2 ? 3 : 2) ragged_kernel(Batc
   // The huge prefix of the length order (messages perm[0 .. huge)) comes
   // first, then warp tiles of 32 messages from counter next_tile[0].
   const int64_t huge = (perm != nullptr && q.huge_count != nullptr) ? *q.huge_count : 0;
-  const int64_t tiles = (b.n - huge + 32 * M - 1) / (32 * M);
+  const int64_t tiles = (b.n - huge + 31) / 32;
   int64_t static_tile = static_cast<int64_t>(blockIdx.x) * WARPS + warp;
   const int64_t static_step = static_cast<int64_t>(gridDim.x) * WARPS;
 
@@ -610,85 +567,42 @@ __global__ void __launch_bounds__(WARPS * 32, M == 2 ? 3 : 2) ragged_kernel(Batc
     }
     if (tile >= tiles) break;
 
-    // Message i of this lane's tile slot: huge + tile * 32 M + 32 i + lane.
-    bool valid[M];
-    int64_t m[M], start[M], len[M];
-    int bad[M];
-    State s[M];
-    bool all_short = true;
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-      const int64_t idx = huge + tile * 32 * M + 32 * i + lane;
-      valid[i] = idx < b.n;
-      m[i] = 0;
-      start[i] = 0;
-      len[i] = 0;
-      bad[i] = 0;
-      if (valid[i]) {
-        m[i] = perm ? static_cast<int64_t>(perm[idx]) : idx;
-        message_bounds(b, m[i], start[i], len[i], bad[i]);
-        if (bad[i]) record_error(b.err, bad[i]);
-      }
-      start_state(b, m[i], valid[i], s[i]);
-      all_short = all_short && len[i] <= 64;
+    const int64_t idx = huge + tile * 32 + lane;
+    const bool valid = idx < b.n;
+    int64_t m = 0, start = 0, len = 0;
+    int bad = 0;
+    if (valid) {
+      m = perm ? static_cast<int64_t>(perm[idx]) : idx;
+      message_bounds(b, m, start, len, bad);
+      if (bad) record_error(b.err, bad);
     }
-    if (__all_sync(kFull, all_short)) {
-#pragma unroll
-      for (int i = 0; i < M; ++i) {
-        hash_short(s[i], base + start[i], static_cast<uint32_t>(len[i]), base + lo, base + hi);
-        end_state(b, m[i], valid[i], bad[i], s[i]);
-      }
+    State s;
+    start_state(b, m, valid, s);
+    if (__all_sync(kFull, len <= 64)) {
+      hash_short(s, base + start, static_cast<uint32_t>(len), base + lo, base + hi);
+      end_state(b, m, valid, bad, s);
       continue;
     }
-    int64_t my_steps[M], packets[M], rem_step[M];
-    uintptr_t msg[M];
-    uint32_t mis[M], r[M];
-    int64_t longest = 0;
-    bool all_aligned = true;
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-      my_steps[i] = (len[i] + W - 1) / W;
-      longest = my_steps[i] > longest ? my_steps[i] : longest;
-      msg[i] = base + start[i];
-      mis[i] = static_cast<uint32_t>(msg[i] & 15);
-      all_aligned = all_aligned && (mis[i] == 0 || !valid[i]);
-      packets[i] = len[i] >> 5;
-      r[i] = static_cast<uint32_t>(len[i] & 31);
-      rem_step[i] = r[i] ? (packets[i] * 32) / W : -1;
-    }
-    const int64_t steps = warp_max(longest);
-    const bool aligned = __all_sync(kFull, all_aligned);
-    WarpStager<W, NST, M> stager{ring, ring_s, {}, {}, {}, {}, safe_lo, safe_hi, lane};
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-      stager.msg[i] = msg[i];
-      stager.len[i] = len[i];
-      stager.my_steps[i] = my_steps[i];
-      stager.my_row[i] = 32 * i + spread_row(aligned, valid[i], mis[i], lane);
-    }
-    stager.run(steps, [&](int64_t k, const uint8_t* stage) {
-      const uint8_t* row[M];
-#pragma unroll
-      for (int i = 0; i < M; ++i) row[i] = stage + stager.my_row[i] * L::kStride;
-      if (M == 2 && (k + 1) * (W / 32) <= packets[0] && (k + 1) * (W / 32) <= packets[M - 1]) {
+    const int64_t my_steps = (len + W - 1) / W;
+    const int64_t steps = warp_max(my_steps);
+    const uintptr_t msg = base + start;
+    const uint32_t mis = static_cast<uint32_t>(msg & 15);
+    const bool aligned = __all_sync(kFull, mis == 0 || !valid);
+    const int64_t packets = len >> 5;
+    const uint32_t r = static_cast<uint32_t>(len & 31);
+    const int64_t rem_step = r ? (packets * 32) / W : -1;
+    const WarpStager<W, NST> stager{ring, ring_s, msg, len, my_steps,
+                                    spread_row(aligned, valid, mis, lane), safe_lo, safe_hi,
+                                    lane};
+    stager.run(steps, [&](int64_t k, const uint8_t* row) {
+      if (k < my_steps) {
         if (aligned)  // warp-uniform
-          hash_full2<W, true>(s[0], row[0], 0u, s[M - 1], row[M - 1], 0u);
+          hash_step<W, true>(s, row, 0u, k, packets, r, rem_step, 1u);
         else
-          hash_full2<W, false>(s[0], row[0], mis[0], s[M - 1], row[M - 1], mis[M - 1]);
-        return;
-      }
-#pragma unroll
-      for (int i = 0; i < M; ++i) {
-        if (k < my_steps[i]) {
-          if (aligned)
-            hash_step<W, true>(s[i], row[i], 0u, k, packets[i], r[i], rem_step[i], 1u);
-          else
-            hash_step<W, false>(s[i], row[i], mis[i], k, packets[i], r[i], rem_step[i], 1u);
-        }
+          hash_step<W, false>(s, row, mis, k, packets, r, rem_step, 1u);
       }
     });
-#pragma unroll
-    for (int i = 0; i < M; ++i) end_state(b, m[i], valid[i], bad[i], s[i]);
+    end_state(b, m, valid, bad, s);
     __syncwarp();
   }
   // The last warp of a launch with huge messages leaves g_huge_kernels.
@@ -850,11 +764,11 @@ __global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, co
   }
 }
 
-template <int W, int NST, int WARPS, int M>
+template <int W, int NST, int WARPS>
 cudaError_t launch_ragged_t(const Batch& b, const Queue& q, int num_sms, cudaStream_t stream) {
-  using L = RaggedLayout<W, NST, M>;
+  using L = RaggedLayout<W, NST>;
   constexpr int kBytes = WARPS * L::kWarpBytes;
-  auto kern = ragged_kernel<W, NST, WARPS, M>;
+  auto kern = ragged_kernel<W, NST, WARPS>;
   cudaError_t e;
   const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), WARPS * 32, kBytes, &e);
   if (e != cudaSuccess) return e;
@@ -882,8 +796,8 @@ cudaError_t launch_short(const Batch& b, const int* run_if, int num_sms, cudaStr
 }
 
 bool ragged_shape_valid(StagedShape shape) {
-#define HH_VALID(W_, N_, M_) \
-  if (shape.window == W_ && shape.stages == N_ && shape.msgs == M_) return true;
+#define HH_VALID(W_, N_) \
+  if (shape.window == W_ && shape.stages == N_) return true;
   HH_RAGGED_SHAPES(HH_VALID)
 #undef HH_VALID
   return false;
@@ -891,9 +805,8 @@ bool ragged_shape_valid(StagedShape shape) {
 
 cudaError_t launch_ragged(const Batch& b, const Queue& q, StagedShape shape, int num_sms,
                           cudaStream_t stream) {
-#define HH_RAGGED(W_, N_, M_)                                             \
-  if (shape.window == W_ && shape.stages == N_ && shape.msgs == M_)     \
-    return launch_ragged_t<W_, N_, kRaggedWarps, M_>(b, q, num_sms, stream);
+#define HH_RAGGED(W_, N_) \
+  if (shape.window == W_ && shape.stages == N_) return launch_ragged_t<W_, N_, kRaggedWarps>(b, q, num_sms, stream);
   HH_RAGGED_SHAPES(HH_RAGGED)
 #undef HH_RAGGED
   return cudaErrorInvalidValue;

@@ -250,11 +250,10 @@ __global__ void __launch_bounds__(WARPS * 32, 3) siptree_kernel(Batch b, Queue q
       const uint32_t mis = static_cast<uint32_t>(msg & 15);
       const bool aligned = __all_sync(kFull, mis == 0 || !valid);
       const int64_t rem_step = r ? (whole * 32) / W : -1;
-      const WarpStager<W, NST> stager{ring, ring_s, {msg}, {len}, {my_steps},
-                                      {spread_row(aligned, valid, mis, lane)}, safe_lo, safe_hi,
+      const WarpStager<W, NST> stager{ring, ring_s, msg, len, my_steps,
+                                      spread_row(aligned, valid, mis, lane), safe_lo, safe_hi,
                                       lane};
-      stager.run(steps, [&](int64_t k, const uint8_t* stage) {
-        const uint8_t* row = stage + stager.my_row[0] * RaggedLayout<W, NST>::kStride;
+      stager.run(steps, [&](int64_t k, const uint8_t* row) {
         if (k < my_steps) {
           if (aligned)  // warp-uniform
             tree_step<W, true, C>(t, row, 0u, k, whole, r, rem_step);

@@ -22,14 +22,12 @@ namespace hh {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// M messages per lane: a stage holds 32 M rows (row 32 i + l is message i of
-// lane l's row set).
-template <int W, int NST, int M = 1>
+template <int W, int NST>
 struct RaggedLayout {
   static constexpr int kStride = W + 16;             // bytes per row
   static constexpr int kChunks = kStride / 16;       // 16-byte chunks per row
   static constexpr int kPerLane = (kChunks + 3) / 4; // chunks per lane per row
-  static constexpr int kStageBytes = 32 * M * kStride;
+  static constexpr int kStageBytes = 32 * kStride;
   static constexpr int kWarpBytes = NST * kStageBytes + 64;  // + read-past pad
   static_assert((kStride / 4) % 32 == 4, "row stride must rotate 128-bit banks");
 };
@@ -139,108 +137,93 @@ __device__ __forceinline__ int spread_row(bool tile_aligned, bool valid, uint32_
 }
 
 // Copies the windows of a warp tile into the warp's ring (see the header).
-// Each lane owns M messages; message i of lane l lives in row my_row[i], one
-// of rows 32 i .. 32 i + 31.
-template <int W, int NST, int M = 1>
+template <int W, int NST>
 struct WarpStager {
-  using L = RaggedLayout<W, NST, M>;
-  uint8_t* ring;        // the warp's ring (generic address)
-  uint32_t ring_s;      // ... and its shared address
-  uintptr_t msg[M];     // this lane's message starts
-  int64_t len[M];       // ... their lengths
-  int64_t my_steps[M];  // windows each has
-  int my_row[M];        // rows in every stage
-  uintptr_t safe_lo;    // 16-byte aligned part of the batch's byte range
+  using L = RaggedLayout<W, NST>;
+  uint8_t* ring;       // the warp's ring (generic address)
+  uint32_t ring_s;     // ... and its shared address
+  uintptr_t msg;       // this lane's message start
+  int64_t len;         // ... its length
+  int64_t my_steps;    // windows it has
+  int my_row;          // its row in every stage
+  uintptr_t safe_lo;   // 16-byte aligned part of the batch's byte range
   uintptr_t safe_hi;
   int lane;
 
-  // Stage k of all 32 M messages into ring buffer `buf`, as one cp.async group.
+  // Stage k of all 32 messages into ring buffer `buf`, as one cp.async group.
   __device__ __forceinline__ void issue(int64_t k, int buf) const {
     const int part = lane & 3, row_in_pass = lane >> 2;
     // When every row's window lies inside its message and the row's whole
     // 16-byte aligned span inside the batch, all rows copy every chunk
     // (bytes past a window land in the row's slack and are never hashed).
-    uintptr_t a0_full[M];
-    bool row_full = true;
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-      a0_full[i] = (msg[i] + static_cast<uintptr_t>(k) * W) & ~uintptr_t(15);
-      row_full = row_full && k < my_steps[i] && (k + 1) * W <= len[i] &&
-                 a0_full[i] >= safe_lo && a0_full[i] + L::kStride <= safe_hi;
-    }
+    const uintptr_t a0_full = (msg + static_cast<uintptr_t>(k) * W) & ~uintptr_t(15);
+    const bool row_full = k < my_steps && (k + 1) * W <= len && a0_full >= safe_lo &&
+                          a0_full + L::kStride <= safe_hi;
     if (__all_sync(kFull, row_full)) {
 #pragma unroll
-      for (int i = 0; i < M; ++i) {
+      for (int h = 0; h < 4; ++h) {
+        const int owner = 8 * h + row_in_pass;
+        const uintptr_t rbase = static_cast<uintptr_t>(
+            __shfl_sync(kFull, static_cast<unsigned long long>(a0_full), owner));
+        const int row = __shfl_sync(kFull, my_row, owner);
+        const char* src = reinterpret_cast<const char*>(rbase) + 16 * part;
+        const uint32_t dst = ring_s + buf * L::kStageBytes + row * L::kStride + 16 * part;
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const int owner = 8 * h + row_in_pass;
-          const uintptr_t rbase = static_cast<uintptr_t>(
-              __shfl_sync(kFull, static_cast<unsigned long long>(a0_full[i]), owner));
-          const int row = __shfl_sync(kFull, my_row[i], owner);
-          const char* src = reinterpret_cast<const char*>(rbase) + 16 * part;
-          const uint32_t dst = ring_s + buf * L::kStageBytes + row * L::kStride + 16 * part;
-#pragma unroll
-          for (int c = 0; c < L::kPerLane; ++c)
-            if (c + 1 < L::kPerLane || part + 4 * c < L::kChunks)
-              cp_async16(dst + 64 * c, src + 64 * c);
-        }
+        for (int i = 0; i < L::kPerLane; ++i)
+          if (i + 1 < L::kPerLane || part + 4 * i < L::kChunks)
+            cp_async16(dst + 64 * i, src + 64 * i);
       }
       cp_async_commit();
       return;
     }
     uint8_t* stage = ring + buf * L::kStageBytes;
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-      // Owner side: this lane's window of message i, as a 16-byte aligned
-      // chunk range.
-      uintptr_t a0 = 0;
-      uint32_t range = 0;  // first valid chunk | (end chunk << 8)
-      if (k < my_steps[i]) {
-        const uintptr_t gs = msg[i] + static_cast<uintptr_t>(k) * W;
-        const int64_t wend = k * W + W < len[i] ? k * W + W : len[i];
-        const uintptr_t ge = msg[i] + static_cast<uintptr_t>(wend);
-        a0 = gs & ~uintptr_t(15);
-        const uintptr_t a1 = (ge + 15) & ~uintptr_t(15);
-        const uintptr_t c0 = a0 > safe_lo ? a0 : safe_lo;
-        const uintptr_t c1 = a1 < safe_hi ? a1 : safe_hi;
-        uint32_t first = 0, end = 0;
-        if (c1 > c0) {
-          first = static_cast<uint32_t>((c0 - a0) >> 4);
-          end = static_cast<uint32_t>((c1 - a0) >> 4);
-        }
-        range = first | (end << 8);
-        if (c0 > gs || c1 < ge || c1 <= c0) {
-          // Bytes in the partial blocks at the batch ends: read bytewise.
-          uint8_t* row = stage + my_row[i] * L::kStride;
-          for (uintptr_t p = gs; p < ge; ++p)
-            if (p < c0 || p >= c1 || c1 <= c0) row[p - a0] = *reinterpret_cast<const uint8_t*>(p);
-        }
+    // Owner side: this lane's window, as a 16-byte aligned chunk range.
+    uintptr_t a0 = 0;
+    uint32_t range = 0;  // first valid chunk | (end chunk << 8)
+    if (k < my_steps) {
+      const uintptr_t gs = msg + static_cast<uintptr_t>(k) * W;
+      const int64_t wend = k * W + W < len ? k * W + W : len;
+      const uintptr_t ge = msg + static_cast<uintptr_t>(wend);
+      a0 = gs & ~uintptr_t(15);
+      const uintptr_t a1 = (ge + 15) & ~uintptr_t(15);
+      const uintptr_t c0 = a0 > safe_lo ? a0 : safe_lo;
+      const uintptr_t c1 = a1 < safe_hi ? a1 : safe_hi;
+      uint32_t first = 0, end = 0;
+      if (c1 > c0) {
+        first = static_cast<uint32_t>((c0 - a0) >> 4);
+        end = static_cast<uint32_t>((c1 - a0) >> 4);
       }
-      // Copier side: four lanes per message, eight messages per pass.
+      range = first | (end << 8);
+      if (c0 > gs || c1 < ge || c1 <= c0) {
+        // Bytes in the partial blocks at the batch ends: read bytewise.
+        uint8_t* row = stage + my_row * L::kStride;
+        for (uintptr_t p = gs; p < ge; ++p)
+          if (p < c0 || p >= c1 || c1 <= c0) row[p - a0] = *reinterpret_cast<const uint8_t*>(p);
+      }
+    }
+    // Copier side: four lanes per message, eight messages per pass.
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const int owner = 8 * h + row_in_pass;
-        const uintptr_t rbase = static_cast<uintptr_t>(
-            __shfl_sync(kFull, static_cast<unsigned long long>(a0), owner));
-        const uint32_t rr = __shfl_sync(kFull, range, owner);
-        const int row = __shfl_sync(kFull, my_row[i], owner);
-        const uint32_t first = rr & 0xff, end = rr >> 8;
-        const char* src = reinterpret_cast<const char*>(rbase) + 16 * part;
-        const uint32_t dst = ring_s + buf * L::kStageBytes + row * L::kStride + 16 * part;
+    for (int h = 0; h < 4; ++h) {
+      const int owner = 8 * h + row_in_pass;
+      const uintptr_t rbase = static_cast<uintptr_t>(
+          __shfl_sync(kFull, static_cast<unsigned long long>(a0), owner));
+      const uint32_t rr = __shfl_sync(kFull, range, owner);
+      const int row = __shfl_sync(kFull, my_row, owner);
+      const uint32_t first = rr & 0xff, end = rr >> 8;
+      const char* src = reinterpret_cast<const char*>(rbase) + 16 * part;
+      const uint32_t dst = ring_s + buf * L::kStageBytes + row * L::kStride + 16 * part;
 #pragma unroll
-        for (int c = 0; c < L::kPerLane; ++c) {
-          const uint32_t ch = part + 4 * c;
-          if (ch >= first && ch < end) cp_async16(dst + 64 * c, src + 64 * c);
-        }
+      for (int i = 0; i < L::kPerLane; ++i) {
+        const uint32_t c = part + 4 * i;
+        if (c >= first && c < end) cp_async16(dst + 64 * i, src + 64 * i);
       }
     }
     cp_async_commit();
   }
 
   // Runs the ring over `steps` windows (the warp's longest message): stage
-  // k + NST - 1 is copied while stage k is hashed by step(k, stage), which
-  // every lane calls for every k (stage: the stage's first byte; this lane's
-  // rows are stage + my_row[i] * kStride).
+  // k + NST - 1 is copied while stage k is hashed by step(k, row), which
+  // every lane calls for every k (its own row in stage k).
   template <typename Step>
   __device__ __forceinline__ void run(int64_t steps, Step&& step) const {
     int buf_issue = 0, buf_read = 0;
@@ -255,7 +238,7 @@ struct WarpStager {
       buf_issue = (buf_issue + 1 == NST) ? 0 : buf_issue + 1;
       cp_async_wait<NST - 1>();
       __syncwarp();
-      step(k, ring + buf_read * L::kStageBytes);
+      step(k, ring + buf_read * L::kStageBytes + my_row * L::kStride);
       __syncwarp();  // every lane is done with this buffer before it refills
       buf_read = (buf_read + 1 == NST) ? 0 : buf_read + 1;
     }

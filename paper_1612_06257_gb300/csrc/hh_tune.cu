@@ -130,7 +130,7 @@ uint64_t next_random(uint64_t& state) {
 #define HH_LIST(W_, N_, M_) hh::StagedShape{W_, N_, M_},
 const hh::StagedShape kFixedCandidates[] = {HH_FIXED_SHAPES(HH_LIST)};
 #undef HH_LIST
-#define HH_LIST(W_, N_, M_) hh::StagedShape{W_, N_, M_},
+#define HH_LIST(W_, N_) hh::StagedShape{W_, N_, 1},
 const hh::StagedShape kRaggedCandidates[] = {HH_RAGGED_SHAPES(HH_LIST)};
 #undef HH_LIST
 
@@ -323,8 +323,8 @@ int hh_tune_describe(hh_ctx* ctx, char* buf, int64_t buf_len) {
     std::snprintf(line, sizeof(line), "fixed %d %d %d %d\n", c, f.window, f.stages, f.msgs);
     text += line;
   }
-  std::snprintf(line, sizeof(line), "ragged %d %d %d\n", ctx->tune.ragged.window,
-                ctx->tune.ragged.stages, ctx->tune.ragged.msgs);
+  std::snprintf(line, sizeof(line), "ragged %d %d\n", ctx->tune.ragged.window,
+                ctx->tune.ragged.stages);
   text += line;
   std::snprintf(line, sizeof(line), "huge_bucket %d\n", ctx->tune.huge_bucket);
   text += line;
@@ -402,9 +402,7 @@ bool load_tune_table(const char* path, TuneTable& t) {
       ok = c >= 0 && c < kFixedClasses && fixed_shape_valid(sh);
       if (ok) parsed.fixed[c] = sh;
     } else if (std::sscanf(line, "ragged %d %d", &w, &n) == 2) {
-      int per = 1;  // messages per lane (a two-number line is from an older table)
-      std::sscanf(line, "ragged %d %d %d", &w, &n, &per);
-      const StagedShape sh{w, n, per};
+      const StagedShape sh{w, n, 1};
       ok = ragged_shape_valid(sh);
       if (ok) parsed.ragged = sh;
     } else {

@@ -460,39 +460,3 @@ def test_fixed_batches_either_side_of_the_two_threads_per_message_size(ctx):
             idx = np.unique(np.concatenate([np.arange(0, n, 97), [n - 1, n - 2]]))
             assert np.array_equal(got[idx], oracle_hashes(w, bits, indices=idx)), (n, length)
 
-
-# ------------------------------------------------- two messages per lane
-
-@pytest.fixture(scope="module")
-def ctx_m2():
-    c = hh.hh_init(0)
-    hh.hh_set_staged_shape(c, hh.HH_REGIME_RAGGED, 128, 2, 2)
-    yield c
-    hh.hh_destroy(c)
-
-
-def test_two_messages_per_lane_every_length(ctx_m2):
-    """Warp tiles of 64 (two messages per lane, interleaved when both have a
-    full window): every length 0..1024 twice, shuffled."""
-    g = torch.Generator().manual_seed(51)
-    lengths = torch.cat([torch.arange(1025), torch.arange(1025)])
-    lengths = lengths[torch.randperm(lengths.numel(), generator=g)]
-    w = workloads.from_lengths(lengths, seed=51, device=DEV, per_message_keys=True)
-    for kernel in ("auto", "unsorted"):
-        assert np.array_equal(run_ragged(ctx_m2, w, 128, kernel), oracle_hashes(w, 128))
-
-
-def test_two_messages_per_lane_loguniform_and_long(ctx_m2):
-    w = workloads.ragged(16384, seed=52, device=DEV)
-    assert np.array_equal(run_ragged(ctx_m2, w, 64), oracle_hashes(w, 64))
-    lengths = torch.cat([torch.randint(0, 5000, (3000,), generator=torch.Generator().manual_seed(53)),
-                         torch.tensor([(1 << 17) + 9, 300000, (1 << 20) + 3])])
-    w = workloads.from_lengths(lengths, seed=53, device=DEV)
-    assert np.array_equal(run_ragged(ctx_m2, w, 256), oracle_hashes(w, 256))
-
-
-def test_two_messages_per_lane_aligned_fixed_and_short(ctx_m2):
-    w = workloads.fixed(5000, 1024, seed=54, device=DEV)
-    assert np.array_equal(run_ragged(ctx_m2, w, 64), oracle_hashes(w, 64))
-    w = workloads.short(6000, seed=55, device=DEV)
-    assert np.array_equal(run_ragged(ctx_m2, w, 64), oracle_hashes(w, 64))
