@@ -123,3 +123,15 @@ def test_edge_cases(ctx):
     assert got[1] == 0
     expect = oracle_tree(w, "siptree")
     assert got[0] == expect[0] and got[3] == expect[3]
+
+
+@pytest.mark.parametrize("name", sorted(VARIANTS))
+def test_long_messages_beside_short_ones(ctx, name):
+    """Messages of 128 KiB to 1 MiB + 13 B (thousands of staged windows each)
+    among short and medium ones, per-message keys, unaligned starts."""
+    g = torch.Generator().manual_seed(46)
+    lengths = torch.cat([torch.randint(0, 4000, (600,), generator=g),
+                         torch.tensor([1 << 17, (1 << 17) + 1, 300001, (1 << 20) + 13])])
+    lengths = lengths[torch.randperm(lengths.numel(), generator=g)]
+    w = workloads.from_lengths(lengths, seed=46, device=DEV, per_message_keys=True)
+    assert np.array_equal(gpu_tree(ctx, w, name), oracle_tree(w, name))
