@@ -9,7 +9,12 @@ The inputs (1 GiB) are larger than L2 (129 MB), so no flush is needed.
   python bench.py --workload small|ragged|short|serving|prng|stats
   python bench.py --workload oracle      (CPU only: the oracle on one thread)
 
-Rank 0 prints one JSON line.  --impl reference times the CPU oracle (the
+Rank 0 prints one JSON line.  Besides the headline step it carries, under
+`extra`, the other shapes of the same metric measured in the same run, each
+with its own clock record: 4096 x 1 KiB (microseconds per batch), 2^22
+log-uniform ragged messages (HBM roofline), 2^26 messages of 0..64 B
+(integer-issue roofline), the serving loop (p50/p99 at two loads) and
+SipTreeHash beside HighwayHash.  --impl reference times the CPU oracle (the
 scalar C implementation the tests check against) on the host cores instead.
 """
 from __future__ import annotations
@@ -49,7 +54,8 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra-configs", action="store_true",
-                   help="skip the ragged, short and SipTreeHash figures (extra.*)")
+                   help="skip the small, ragged, short, serving and SipTreeHash figures "
+                        "(extra.*)")
     p.add_argument("--workload", default=None,
                    choices=["small", "ragged", "short", "serving", "prng", "stats", "siptree",
                             "oracle"],
@@ -67,7 +73,7 @@ class ClockSampler:
                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
                0x2: "applications_clocks_setting", 0x100: "display_clock_setting"}
 
-    def __init__(self, torch_device: int, period_s: float = 0.005):
+    def __init__(self, torch_device: int, period_s: float = 0.001):
         import torch
         self.period = period_s
         self.samples = []
@@ -368,8 +374,11 @@ def run_ours(args, rank, world, local_rank):
                 "launch_ms": round(launch_ms, 4)}
 
     extra = {}
-    # Other output widths and the plain one-message-per-thread kernel, timed
-    # on the same batch after the main region (a few steps each).
+    # Other output widths, the plain one-message-per-thread kernel and the
+    # end-to-end figure, timed on the same batch after the main region (a few
+    # steps each), under a clock record of their own.
+    other_clocks = ClockSampler(local_rank)
+    other_clocks.start()
     reps = max(3, min(K, 20))
     for bits in (128, 256):
         o = torch.empty(N_MESSAGES * bits // 64, dtype=torch.int64, device=dev)
@@ -426,6 +435,8 @@ def run_ours(args, rank, world, local_rank):
         w.data.copy_(host_data, non_blocking=True)
         torch.cuda.synchronize()
         copy_s.append(time.perf_counter() - t0)
+    other_clocks.stop()
+    extra["clocks_widths_naive_e2e"] = other_clocks.summary()
     e2e = {"value": round(world * payload / e2e_s / 1e9, 2), "unit": "GB/s",
            "h2d_bytes_per_step": payload + 8 * (N_MESSAGES + 1) + 32,
            "d2h_bytes_per_step": 8 * N_MESSAGES,
@@ -433,14 +444,19 @@ def run_ours(args, rank, world, local_rank):
            "h2d_copy_gbs": round(payload / min(copy_s) / 1e9, 1)}
 
     # The other configurations of the same metric, each with its own clock
-    # record: config 3 (2^22 log-uniform ragged messages, per-message keys:
-    # HBM roofline), config 4 (2^26 messages of 0..64 B: integer-issue
-    # roofline), and SipTreeHash beside HighwayHash on this batch.
+    # record: 4096 x 1 KiB (latency: microseconds per batch), 2^22
+    # log-uniform ragged messages with per-message keys (HBM roofline), 2^26
+    # messages of 0..64 B (integer-issue roofline), the serving loop (p50/p99
+    # at two loads, 256 requests each; the full sweep is bench.py --workload
+    # serving), and SipTreeHash beside HighwayHash on this batch.
     if not args.no_extra_configs:
         from paper_1612_06257_gb300 import bench_workloads
         torch.cuda.empty_cache()
-        for name, fn in (("ragged", lambda: bench_workloads.ragged(ctx, dev, naive_reps=1)),
+        for name, fn in (("small", lambda: bench_workloads.small(ctx, dev)),
+                         ("ragged", lambda: bench_workloads.ragged(ctx, dev, naive_reps=1)),
                          ("short", lambda: bench_workloads.short(ctx, dev)),
+                         ("serving", lambda: bench_workloads.serving(ctx, dev, requests=256,
+                                                                     rates=(0.3, 0.7))),
                          ("siptree", lambda: bench_workloads.siptree(ctx, dev, w))):
             s = ClockSampler(local_rank)
             s.start()
