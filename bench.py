@@ -374,6 +374,18 @@ def run_ours(args, rank, world, local_rank):
                 "launch_ms": round(launch_ms, 4)}
 
     extra = {}
+    # The timed region of a short run holds only a few clock samples; the
+    # same step repeated for about 0.3 s right after it shows the clocks
+    # under that load with many samples (not timed, not part of `value`).
+    soak = ClockSampler(local_rank)
+    soak.start()
+    t_soak = time.perf_counter()
+    while time.perf_counter() - t_soak < 0.3:
+        for _ in range(100):
+            step()
+        torch.cuda.synchronize()
+    soak.stop()
+    extra["clocks_same_step_soak"] = soak.summary()
     # Other output widths, the plain one-message-per-thread kernel and the
     # end-to-end figure, timed on the same batch after the main region (a few
     # steps each), under a clock record of their own.
