@@ -44,6 +44,15 @@ def _peak_hbm():
         return 6800.0, "fallback"
 
 
+def _max_sm_clock_hz():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    try:
+        with open(os.path.join(root, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"]) * 1e6
+    except (OSError, KeyError, ValueError):
+        return 2070e6  # GB300 maximum SM clock
+
+
 def _time(fn, reps, flush=None):
     fn()
     torch.cuda.synchronize()
@@ -236,6 +245,26 @@ def siptree(ctx, dev, w=None):
         ms, _ = _time(fn, 10)
         res["%s_gbps" % name] = round(w.total_bytes / ms / 1e6, 1)
         res["%s_ms" % name] = round(ms, 4)
+    # Integer-ALU roofline: a SipRound is 24 ALU instructions (4 64-bit adds,
+    # 4 rotations of two funnel shifts, 4 64-bit xors; the 32-bit rotations
+    # are free) and a compression adds 4 xors.  Per message of L bytes with P
+    # = L / 32 vectors: 4 P (24 c + 4) for the lanes, 4 (24 (c + d) + 4) for
+    # their last word and finalisation, and (6 c + d) 24 + 28 for the fold.
+    # The ALU pipe retires 16 lanes per clock per SM sub-partition.
+    props = torch.cuda.get_device_properties(dev)
+    sm_hz = _max_sm_clock_hz()
+    alu_peak = 16 * 4 * props.multi_processor_count * sm_hz  # ALU lane-instructions per second
+    length = w.fixed_len or int(w.total_bytes // max(1, w.n))
+    vectors = (length + 31) // 32
+    for name, (c, d) in (("siptree", (2, 4)), ("siptree13", (1, 3))):
+        alu = 4 * vectors * (24 * c + 4) + 4 * (24 * (c + d) + 4) + (6 * c + d) * 24 + 28
+        ceiling = alu_peak / alu * length / 1e9  # GB/s of payload
+        res["%s_roofline" % name] = {
+            "bound": "alu", "achieved": res["%s_gbps" % name], "peak": round(ceiling, 1),
+            "unit": "GB/s", "frac": round(res["%s_gbps" % name] / ceiling, 4),
+            "alu_instructions_per_message": alu, "sm_clock_hz": sm_hz,
+            "peak_source": "derived: 16 ALU lanes/clk per SM sub-partition x 4 x SMs x "
+                           "max SM clock / ALU instructions per message"}
     res["highwayhash_over_siptree"] = round(res["highwayhash_gbps"] / res["siptree_gbps"], 2)
     res["highwayhash_over_siptree13"] = round(res["highwayhash_gbps"] / res["siptree13_gbps"], 2)
     # Table 1 at 1024 B (cycles per byte on one Haswell core): SipTreeHash
