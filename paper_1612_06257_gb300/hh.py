@@ -164,6 +164,8 @@ def hh_destroy(ctx: Context) -> None:
 
 
 def hh_reserve(ctx: Context, max_messages: int) -> None:
+    """Size the context's sort scratch for batches of up to max_messages (the
+    hash calls never allocate; beyond it they raise HH_ERR_TOO_LARGE)."""
     _check(load_library().hh_reserve(ctx.ptr, int(max_messages)), "hh_reserve")
 
 
