@@ -46,6 +46,12 @@ WORKLOAD = ("HighwayHash-64, 2^20 messages x 1024 B of uniform random bytes (1 G
 OUT_BYTES = 8
 
 
+def workload_config() -> dict:
+    """The configuration both arms measure (the GPU arm adds how it ran)."""
+    return {"workload": WORKLOAD, "n_messages": N_MESSAGES, "message_bytes": MESSAGE_BYTES,
+            "bits": 64, "key": "shared"}
+
+
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -483,10 +489,9 @@ def run_ours(args, rank, world, local_rank):
         "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded uniform random bytes and key, generated on device)",
-        "config": {"workload": WORKLOAD, "n_messages": N_MESSAGES,
-                   "message_bytes": MESSAGE_BYTES, "bits": 64, "key": "shared",
-                   "api": "hh_hash_fixed", "l2": "inputs (1 GiB) larger than L2 (129 MB); no flush",
-                   "parallelism": "replica per GPU" if world > 1 else "single GPU"},
+        "config": dict(workload_config(),
+                       api="hh_hash_fixed", l2="inputs (1 GiB) larger than L2 (129 MB); no flush",
+                       parallelism="replica per GPU" if world > 1 else "single GPU"),
         "hashes_per_s": round(hashes_per_s, 1),
         "roofline": roofline,
         "e2e": e2e,
@@ -534,8 +539,7 @@ def run_reference(args, rank, world):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded, host)",
-        "config": {"workload": WORKLOAD, "n_messages": N_MESSAGES,
-                   "message_bytes": MESSAGE_BYTES, "bits": 64, "key": "shared"},
+        "config": workload_config(),
         "hashes_per_s": round(N_MESSAGES / sec, 1),
         "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": cores,
                          "kind": "oracle",
