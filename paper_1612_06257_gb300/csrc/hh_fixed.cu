@@ -3,12 +3,11 @@
 // A batch of n messages of `len` bytes (len a multiple of 16, 16-byte aligned
 // base) is a 2D byte tensor [n][len].  A CTA of 128 threads owns tiles of 128
 // consecutive messages (one thread per message, the 1024-bit state in
-// registers).  For each W-byte window of the tile one thread issues W/128
-// tensor loads of a 128-row x 128-byte box (128-byte swizzle) into a shared
-// memory stage; NST stages form a ring guarded by "full" mbarriers (TMA
-// transaction bytes) and "empty" mbarriers (one arrival per warp once it has
-// read the stage).  The stream of (tile, window) pairs runs on across tiles,
-// so the next tile's first windows load while the current one finishes.
+// registers).  Each W-byte window of the tile is W/128 tensor loads of a
+// 128-row x 128-byte box (128-byte swizzle) into a shared-memory stage; NST
+// stages form a ring, each with a "full" mbarrier (TMA transaction bytes).
+// The stream of (tile, window) pairs runs on across tiles, so the next
+// tile's first windows load while the current one finishes.
 //
 // Thread t reads its 32-byte packets from row t of the box: 16-byte chunk c
 // lies at chunk position c ^ (t & 7), so the 8 threads of a quarter-warp hit
@@ -16,26 +15,28 @@
 // the end of a message and rows past the end of the batch are zero-filled by
 // the TMA unit; they are never hashed.
 //
-// Giving up (a barrier wait that runs past its limit) stops that thread's
-// waiting and hashing (it writes zero hashes).  Three rules keep the
-// pipeline sound afterwards:
-//  - a warp arrives on an "empty" barrier only while its lane 0 is still
-//    live.  The lanes of a warp meet at __syncwarp every step, so a warp can
-//    run ahead of the real phases only once lane 0 has stopped waiting, and
-//    from then on it no longer arrives: every arrival means that warp has
-//    finished reading the buffer, and a refill never overwrites data in use
-//    (a warp that stops arriving makes the producer's next "empty" wait run
-//    out, which ends the refills);
-//  - thread 0 refills a buffer only after its own wait for the buffer's
-//    previous load succeeded, so at most one load per buffer is in flight
-//    and no "full" phase is armed twice; after an "empty" wait that ran out
-//    it issues nothing more;
-//  - before the CTA exits, thread 0 works out from its cursor how many loads
-//    it issued and waits (kDrainLimitNs each) for those it did not see land,
-//    load q on buffer q mod NST at phase parity (q / NST) mod 2: at most one
-//    per buffer is outstanding and every earlier phase of its buffer has
-//    completed, so the parity names the phase.  No bulk copy is in flight
-//    when the CTA's shared memory is released.
+// The last warp to finish reading a stage refills it.  Once a warp's lanes
+// have read the stage (they meet at __syncwarp), lane 0 bumps the stage's
+// "done" counter with an acquire-release increment that wraps at the warp
+// count; the warp whose increment completes the count issues the load of
+// window g + NST into the stage.  No thread waits for the others to finish
+// with a stage, only for its data to land.
+//
+// Giving up (a "full" wait that runs past its limit) stops that thread's
+// waiting and hashing (it writes zero hashes).  Two rules keep the pipeline
+// sound afterwards:
+//  - a warp counts itself done only while its lane 0 is live.  A lane that
+//    gave up reads no shared memory again, so every count means that warp
+//    has finished with the stage and a refill never overwrites data in use.
+//    A warp whose lane 0 gave up never counts again: no stage is refilled
+//    after that, and the other warps' waits run out in turn.  A stage's next
+//    load goes out only after every warp saw its previous load land, so at
+//    most one load per stage is in flight and no "full" phase is armed twice;
+//  - the issuer records how many loads went into the stage.  Before the CTA
+//    exits all threads meet, and thread b waits (kDrainLimitNs) for the last
+//    load into stage b at the parity of its number: every earlier load into
+//    that stage has completed, so the parity names the phase.  No bulk copy
+//    is in flight when the CTA's shared memory is released.
 // The limit is a compile-time 2 s in the kernels every call uses; a context
 // with its own limit (hh_set_tune_param "wait_limit_ns") runs separate
 // instantiations that read it from their parameters.
@@ -70,7 +71,7 @@ template <int W, int NST, int M>
 struct FixedLayout {
   static constexpr int kStageBytes = W * kRows * M;
   static constexpr int kBarOffset = NST * kStageBytes;
-  static constexpr int kBytes = kBarOffset + 2 * NST * 8 + 1024;  // + alignment slack
+  static constexpr int kBytes = kBarOffset + NST * 8 + 2 * NST * 4 + 1024;  // + counters, slack
 };
 
 __device__ __forceinline__ void load_swizzled_packet(const uint8_t* box, int row, int chunk,
@@ -82,13 +83,34 @@ __device__ __forceinline__ void load_swizzled_packet(const uint8_t* box, int row
   w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
 }
 
-// Thread 0, before the CTA exits: `issued` loads went out (load q into buffer
-// q mod nst, completing phase q / nst), and it saw loads 0 .. stop_g - 1 land
-// (stop_g < 0: all of them); wait for the others.
-__device__ __forceinline__ void drain_loads(uint64_t* full, int nst, int64_t issued,
-                                            int64_t stop_g) {
-  for (int64_t q = stop_g < 0 ? issued : stop_g; q < issued; ++q)
-    mbar_wait_bounded(&full[q % nst], static_cast<uint32_t>((q / nst) & 1), kDrainLimitNs);
+// The (tile, window) `ahead` windows after (tile, k) in this CTA's stream of
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ... of `steps` windows each.
+__device__ __forceinline__ void advance(int64_t& tile, int64_t& k, int ahead, int64_t steps) {
+  k += ahead;
+  while (k >= steps) {
+    k -= steps;
+    tile += gridDim.x;
+  }
+}
+
+// The shared-memory words beside the "full" barriers: per stage the warps
+// done with its current load, and the number of loads issued into it.
+struct RingCounters {
+  uint32_t* done;
+  uint32_t* loads;
+};
+
+__device__ __forceinline__ RingCounters ring_counters(uint64_t* full, int nst) {
+  uint32_t* w = reinterpret_cast<uint32_t*>(full + nst);
+  return {w, w + nst};
+}
+
+// Every thread, before the CTA exits: thread b < nst waits (bounded) for the
+// last load issued into stage b, the only one that can still be in flight.
+__device__ __forceinline__ void drain_last_loads(uint64_t* full, RingCounters c, int nst, int t) {
+  __syncthreads();
+  if (t < nst && c.loads[t] > 0)
+    mbar_wait_bounded(&full[t], (c.loads[t] - 1) & 1u, kDrainLimitNs);
 }
 
 // M messages per thread: a tile is 128 * M messages; thread t hashes
@@ -101,11 +123,12 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
   using L = FixedLayout<W, NST, M>;
   constexpr int kBoxes = W / 128;
   constexpr int kTileMsgs = kRows * M;
+  constexpr uint32_t kWarps = kRows / 32;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kBarOffset);
-  uint64_t* empty = full + NST;
+  const RingCounters ring = ring_counters(full, NST);
 
   const int t = threadIdx.x, lane = t & 31;
   const int64_t steps = (p.len + W - 1) / W;                 // windows per message (>= 1)
@@ -113,36 +136,32 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = my_tiles * steps;                    // this CTA's (tile, window) stream
 
-  if (t == 0) {
-    prefetch_tensormap(&tmap);
-    for (int i = 0; i < NST; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kRows / 32);
-    }
-    fence_mbar_init();
-  }
-  __syncthreads();
-
-  // Producer cursor (thread 0 only): the (tile, window) of the next load.
-  int64_t p_tile = blockIdx.x, p_k = 0;
-  int p_buf = 0;
-  auto issue_next = [&]() {
-    mbar_arrive_expect_tx(&full[p_buf], L::kStageBytes);
+  auto issue = [&](int64_t ltile, int64_t lk, int buf) {
+    mbar_arrive_expect_tx(&full[buf], L::kStageBytes);
 #pragma unroll
     for (int i = 0; i < M; ++i)
 #pragma unroll
       for (int x = 0; x < kBoxes; ++x)
-        tma_load_2d(smem + p_buf * L::kStageBytes + (i * kBoxes + x) * kBoxBytes, &tmap,
-                    static_cast<int32_t>(p_k * W) + 128 * x,
-                    static_cast<int32_t>(p_tile * kTileMsgs + i * kRows), &full[p_buf]);
-    if (++p_k == steps) {
-      p_k = 0;
-      p_tile += gridDim.x;
-    }
-    p_buf = (p_buf + 1 == NST) ? 0 : p_buf + 1;
+        tma_load_2d(smem + buf * L::kStageBytes + (i * kBoxes + x) * kBoxBytes, &tmap,
+                    static_cast<int32_t>(lk * W) + 128 * x,
+                    static_cast<int32_t>(ltile * kTileMsgs + i * kRows), &full[buf]);
   };
-  if (t == 0)
-    for (int64_t g = 0; g < NST && g < total; ++g) issue_next();
+  if (t == 0) {
+    prefetch_tensormap(&tmap);
+    for (int i = 0; i < NST; ++i) {
+      mbar_init(&full[i], 1);
+      ring.done[i] = 0;
+      ring.loads[i] = 0;
+    }
+    fence_mbar_init();
+    int64_t lt = blockIdx.x, lk = 0;
+    for (int q = 0; q < NST && q < total; ++q) {
+      ring.loads[q] = 1;
+      issue(lt, lk, q);
+      advance(lt, lk, 1, steps);
+    }
+  }
+  __syncthreads();
 
   const int64_t packets = p.len >> 5;
   const uint32_t r = static_cast<uint32_t>(p.len & 31);
@@ -155,8 +174,6 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
   }
   State s[M];
   bool ok = true;
-  int64_t stop_g = -1;   // thread 0: the step at which it gave up (-1: never)
-  bool stopped = false;  // thread 0: an "empty" wait ran out; no further loads
   int b = 0;                // stage buffer of the current window
   uint32_t parity = 0;      // its phase parity
   int64_t g = 0;            // position in this CTA's (tile, window) stream
@@ -175,7 +192,6 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
     for (int64_t k = 0; k < steps; ++k, ++g) {
       if (ok && !mbar_wait_bounded(&full[b], parity, limit)) {
         ok = false;
-        if (t == 0) stop_g = g;
         record_error(p.err, kErrTimeout);
       }
       const uint8_t* stage = smem + b * L::kStageBytes;
@@ -203,16 +219,14 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
         }
       }
       __syncwarp();
-      if (lane == 0 && ok) mbar_arrive(&empty[b]);
-      if (t == 0 && ok && !stopped && g + NST < total) {
-        // Refill this buffer once every warp has read it.
-        if (!mbar_wait_bounded(&empty[b], parity, limit)) {
-          record_error(p.err, kErrTimeout);
-          stopped = true;  // refills stop for good: the cursor must stay in step
-        } else {
-          fence_proxy_async_smem();
-          issue_next();
-        }
+      // The last warp done with this stage loads window g + NST into it.
+      if (lane == 0 && ok && atom_inc_wrap_acq_rel(&ring.done[b], kWarps - 1) == kWarps - 1 &&
+          g + NST < total) {
+        int64_t lt = tile, lk = k;
+        advance(lt, lk, NST, steps);
+        ring.loads[b] = static_cast<uint32_t>((g + NST) / NST + 1);
+        fence_proxy_async_smem();
+        issue(lt, lk, b);
       }
       if (++b == NST) {
         b = 0;
@@ -238,9 +252,7 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
       }
     }
   }
-  // Loads issued but never waited for (only after a timeout) get a bounded
-  // time to land before the CTA exits.
-  if (t == 0) drain_loads(full, NST, (p_tile - blockIdx.x) / gridDim.x * steps + p_k, stop_g);
+  drain_last_loads(full, ring, NST, t);
 }
 
 // Two threads per message, for batches too small to fill the GPU: threads
@@ -248,13 +260,13 @@ __global__ void __launch_bounds__(kRows) fixed_tma_kernel(const __grid_constant_
 // mixes lanes only within a pair), so each thread's Update chain is half
 // as long; they trade v0 in finalisation.  Tiles of ROWS messages (32, 64
 // or 128: the launcher picks the largest that still gives every SM a tile)
-// with the same windows and full/empty barrier protocol as fixed_tma_kernel.
+// with the same windows and stage ring protocol as fixed_tma_kernel.
 template <int W, int NST, int ROWS>
 struct PairLayout {
   static constexpr int kBoxBytes = 128 * ROWS;
   static constexpr int kStageBytes = W * ROWS;
   static constexpr int kBarOffset = NST * kStageBytes;
-  static constexpr int kBytes = kBarOffset + 2 * NST * 8 + 1024;  // + alignment slack
+  static constexpr int kBytes = kBarOffset + NST * 8 + 2 * NST * 4 + 1024;  // + counters, slack
 };
 
 template <int W, int NST, int ROWS, bool kCustom>
@@ -263,13 +275,13 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
   const uint64_t limit = kCustom ? p.wait_ns : kWaitLimitNs;
   using L = PairLayout<W, NST, ROWS>;
   constexpr int kBoxes = W / 128;
-  constexpr int kWarps = 2 * ROWS / 32;
+  constexpr uint32_t kWarps = 2 * ROWS / 32;
   constexpr int kBoxB = L::kBoxBytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::kBarOffset);
-  uint64_t* empty = full + NST;
+  const RingCounters ring = ring_counters(full, NST);
 
   const int t = threadIdx.x, lane = t & 31, row = t >> 1, half = t & 1;
   const int64_t steps = (p.len + W - 1) / W;
@@ -277,33 +289,30 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
   const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = my_tiles * steps;
 
+  auto issue = [&](int64_t ltile, int64_t lk, int buf) {
+    mbar_arrive_expect_tx(&full[buf], L::kStageBytes);
+#pragma unroll
+    for (int x = 0; x < kBoxes; ++x)
+      tma_load_2d(smem + buf * L::kStageBytes + x * kBoxB, &tmap,
+                  static_cast<int32_t>(lk * W) + 128 * x, static_cast<int32_t>(ltile * ROWS),
+                  &full[buf]);
+  };
   if (t == 0) {
     prefetch_tensormap(&tmap);
     for (int i = 0; i < NST; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kWarps);
+      ring.done[i] = 0;
+      ring.loads[i] = 0;
     }
     fence_mbar_init();
+    int64_t lt = blockIdx.x, lk = 0;
+    for (int q = 0; q < NST && q < total; ++q) {
+      ring.loads[q] = 1;
+      issue(lt, lk, q);
+      advance(lt, lk, 1, steps);
+    }
   }
   __syncthreads();
-
-  int64_t p_tile = blockIdx.x, p_k = 0;
-  int p_buf = 0;
-  auto issue_next = [&]() {
-    mbar_arrive_expect_tx(&full[p_buf], L::kStageBytes);
-#pragma unroll
-    for (int x = 0; x < kBoxes; ++x)
-      tma_load_2d(smem + p_buf * L::kStageBytes + x * kBoxB, &tmap,
-                  static_cast<int32_t>(p_k * W) + 128 * x, static_cast<int32_t>(p_tile * ROWS),
-                  &full[p_buf]);
-    if (++p_k == steps) {
-      p_k = 0;
-      p_tile += gridDim.x;
-    }
-    p_buf = (p_buf + 1 == NST) ? 0 : p_buf + 1;
-  };
-  if (t == 0)
-    for (int64_t g = 0; g < NST && g < total; ++g) issue_next();
 
   const int64_t packets = p.len >> 5;
   const uint32_t r = static_cast<uint32_t>(p.len & 31);
@@ -316,8 +325,6 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
   }
   Half s;
   bool ok = true;
-  int64_t stop_g = -1;   // thread 0: the step at which it gave up (-1: never)
-  bool stopped = false;  // thread 0: an "empty" wait ran out; no further loads
   int b = 0;
   uint32_t parity = 0;
   int64_t g = 0;
@@ -332,7 +339,6 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
     for (int64_t k = 0; k < steps; ++k, ++g) {
       if (ok && !mbar_wait_bounded(&full[b], parity, limit)) {
         ok = false;
-        if (t == 0) stop_g = g;
         record_error(p.err, kErrTimeout);
       }
       const uint8_t* stage = smem + b * L::kStageBytes;
@@ -356,15 +362,13 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
         }
       }
       __syncwarp();
-      if (lane == 0 && ok) mbar_arrive(&empty[b]);
-      if (t == 0 && ok && !stopped && g + NST < total) {
-        if (!mbar_wait_bounded(&empty[b], parity, limit)) {
-          record_error(p.err, kErrTimeout);
-          stopped = true;  // refills stop for good: the cursor must stay in step
-        } else {
-          fence_proxy_async_smem();
-          issue_next();
-        }
+      if (lane == 0 && ok && atom_inc_wrap_acq_rel(&ring.done[b], kWarps - 1) == kWarps - 1 &&
+          g + NST < total) {
+        int64_t lt = tile, lk = k;
+        advance(lt, lk, NST, steps);
+        ring.loads[b] = static_cast<uint32_t>((g + NST) / NST + 1);
+        fence_proxy_async_smem();
+        issue(lt, lk, b);
       }
       if (++b == NST) {
         b = 0;
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(2 * ROWS) fixed_pair_kernel(
       }
     }
   }
-  if (t == 0) drain_loads(full, NST, (p_tile - blockIdx.x) / gridDim.x * steps + p_k, stop_g);
+  drain_last_loads(full, ring, NST, t);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,

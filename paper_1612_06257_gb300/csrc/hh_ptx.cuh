@@ -68,6 +68,19 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Increment a shared-memory counter that wraps to 0 after reaching `wrap`;
+// returns the old value.  Acquire-release at CTA scope: the caller's earlier
+// shared-memory accesses happen before the increment, and the thread whose
+// increment comes later in the counter's order sees them.
+__device__ __forceinline__ uint32_t atom_inc_wrap_acq_rel(uint32_t* p, uint32_t wrap) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.cta.shared::cta.inc.u32 %0, [%1], %2;"
+               : "=r"(old)
+               : "r"(smem_u32(p)), "r"(wrap)
+               : "memory");
+  return old;
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
