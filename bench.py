@@ -23,6 +23,7 @@ import argparse
 import re
 import concurrent.futures
 import ctypes
+import gc
 import hashlib
 import json
 import os
@@ -325,6 +326,13 @@ def run_ours(args, rank, world, local_rank):
         hh.hh_hash_fixed(ctx, bits, w.keys, 0, w.data, MESSAGE_BYTES, N_MESSAGES, out=o,
                          stream=stream)
 
+    # Python's garbage collector stays off while anything is timed, as timeit
+    # does: a collection pass over the heap of a process that has loaded
+    # torch takes tens of milliseconds and would land in whichever timed
+    # region it happened to fall in.
+    gc.collect()
+    gc.disable()
+
     for _ in range(args.warmup):
         step()
     launches_per_step = hh.hh_last_launch_count(ctx)
@@ -459,7 +467,8 @@ def run_ours(args, rank, world, local_rank):
            "h2d_bytes_per_step": payload + 8 * (N_MESSAGES + 1) + 32,
            "d2h_bytes_per_step": 8 * N_MESSAGES,
            "api": "hh_hash_host (pinned host buffers, chunked H2D/hash/D2H)",
-           "h2d_copy_gbs": round(payload / min(copy_s) / 1e9, 1)}
+           "h2d_copy_gbs": round(payload / min(copy_s) / 1e9, 1),
+           "python_gc": "off while timing"}
 
     # The other configurations of the same metric, each with its own clock
     # record: 4096 x 1 KiB (latency: microseconds per batch), 2^22
@@ -506,6 +515,7 @@ def run_ours(args, rank, world, local_rank):
         base["matches_gpu"] = bool(np.array_equal(gpu_out, ref_out[:, 0]))
         result["cpu_baseline"] = base
     hh.hh_destroy(ctx)
+    gc.enable()
     if dist:
         dist.destroy_process_group()
     return result
@@ -525,12 +535,15 @@ def run_reference(args, rank, world):
     data = w.data.numpy()
     offs = np.arange(N_MESSAGES + 1, dtype=np.int64) * MESSAGE_BYTES
     cores = os.cpu_count() or 1
+    gc.collect()
+    gc.disable()  # as in our arm: no collection pass inside a timed step
     for _ in range(args.warmup):
         oracle_rate(keys, data, offs, 0, N_MESSAGES, cores)
     times = []
     for _ in range(args.steps):
         t, _ = oracle_rate(keys, data, offs, 0, N_MESSAGES, cores)
         times.append(t)
+    gc.enable()
     sec = statistics.mean(times)
     payload = N_MESSAGES * MESSAGE_BYTES
     value = payload / sec / 1e9
