@@ -212,6 +212,35 @@ def test_short_kernel_flags_decreasing_offsets(ctx, per_message_keys):
     assert np.array_equal(got[others], oracle_hashes(broken, 128, indices=others))
 
 
+def test_short_kernel_offsets_that_jump_back(ctx):
+    """One key, 12000 messages of at most 64 bytes (the short kernel).
+    Decreasing offsets put a valid message before the bytes of the 64
+    messages around it (messages 6409/6410), and make the offset 64 messages
+    on from message 3200 fall below it (messages 3263/3264).  The two
+    descriptors with end < start get zero hashes, every other message the
+    oracle's."""
+    g = torch.Generator().manual_seed(47)
+    lengths = torch.randint(0, 65, (12000,), generator=g)
+    lengths[6400:6416] = 1
+    lengths[3200:3266] = torch.randint(0, 2, (66,), generator=g)
+    w = workloads.from_lengths(lengths, seed=47, device=DEV, per_message_keys=False)
+    off = w.offsets.clone()
+    off[6410] = off[6400] - 20  # 6409 ends before it starts; 6410 lies before its chunk
+    off[6411] = off[6400] - 5
+    off[3264] = off[3200] - 1  # 3263 ends before it starts; chunk 3200..3263 is inverted
+    bad_msgs = [3263, 6409]
+    lens = (off[1:] - off[:-1]).cpu()
+    assert int(lens.max()) <= 64 and all(int(lens[i]) < 0 for i in bad_msgs)
+    assert int((lens < 0).sum()) == len(bad_msgs)
+    broken = workloads.Workload("short", w.data, off, None, w.keys, False, w.n)
+    out = hh.hh_hash64_batch(ctx, w.keys, 0, w.data, off)
+    assert hh.hh_get_device_error(ctx) == hh.HH_ERR_BAD_OFFSETS
+    got = as_u64(out, 1)
+    assert all(int(got[i, 0]) == 0 for i in bad_msgs)
+    others = np.array([i for i in range(w.n) if i not in bad_msgs])
+    assert np.array_equal(got[others], oracle_hashes(broken, 64, indices=others))
+
+
 def test_output_guard_words_untouched(ctx):
     w = workloads.ragged(3000, seed=11, device=DEV, max_len=3000)
     out = torch.full((3000 * 2 + 64,), -0x5A5A5A5A5A5A5A5B, dtype=torch.int64, device=DEV)
