@@ -124,6 +124,39 @@ __device__ __forceinline__ void hash_short_words(State& s, const uint32_t x[17],
   }
 }
 
+// As hash_short_words, reading the 17 staged words from a shared-memory slot:
+// the last packet's nine words are read from word 8 when a whole packet
+// precedes it (no select between the two windows), and the word that holds
+// the final len mod 4 bytes is read at its own index (no select tree).
+__device__ __forceinline__ void hash_short_slot(State& s, const uint32_t* slot, uint32_t b,
+                                                uint32_t len) {
+  const uint32_t sel = 0x3210u + 0x1111u * b;
+  const bool two = len > 32u;
+  const uint32_t r = len & 31u;
+  const uint32_t* lp = slot + (two ? 8 : 0);
+  uint32_t t[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) t[j] = __byte_perm(lp[j], lp[j + 1], sel);
+  const uint32_t whole = r ? (r >> 2) : 8u;
+  const uint32_t wl = whole < 7u ? whole : 7u;
+  const uint32_t last = __byte_perm(lp[wl], lp[wl + 1], sel);
+  const uint32_t keep_last = (1u << (8u * (r & 3u))) - 1u;  // 0 when r mod 4 == 0
+  uint32_t pkt[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) pkt[j] = (static_cast<uint32_t>(j) < whole) ? t[j] : 0u;
+  pkt[7] |= last & keep_last;
+  if (two) {
+    uint32_t f[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) f[j] = __byte_perm(slot[j], slot[j + 1], sel);
+    update_words(s, f);
+  }
+  if (len != 0u) {
+    inject_size(s, r);
+    update_words(s, pkt);
+  }
+}
+
 __device__ __forceinline__ void hash_short(State& s, uintptr_t msg, uint32_t len, uintptr_t lo_b,
                                            uintptr_t hi_b) {
   uint32_t x[17];
@@ -731,9 +764,6 @@ __global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, co
     const int bad = e0 < s0 ? kErrBadOffsets : 0;
     int64_t len = bad ? 0 : e0 - s0;
     len = len < kShortMax ? len : kShortMax;
-    uint32_t x[17];
-#pragma unroll
-    for (int i = 0; i < 17; ++i) x[i] = next_words[cur][17 * tid + i];
     const bool more = m + stride < b.n;
     if (more) fetch_offsets(m + stride, cur ^ 1);
     if (bad) record_error(b.err, bad);
@@ -753,7 +783,8 @@ __global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, co
         s.mul1[2 * i + 1] = join(e.z, e.w);
       }
     }
-    hash_short_words(s, x, static_cast<uint32_t>((base + s0) & 3), static_cast<uint32_t>(len));
+    hash_short_slot(s, &next_words[cur][17 * tid], static_cast<uint32_t>((base + s0) & 3),
+                    static_cast<uint32_t>(len));
     if (more) {
       cp_async_wait<0>();
       fetch_words(cur ^ 1);
