@@ -645,15 +645,20 @@ __global__ void __launch_bounds__(WARPS * 32, 2) ragged_kernel(Batch b, Queue q)
 }
 
 // The hash of message m from its finalised state (zero for an invalid
-// descriptor).  Only the lanes that are stored are summed (for 64-bit
-// output, one).
+// descriptor): kWords output words (b.words), or b.words read at run time
+// when kWords is 0.  With kWords known, only lanes 0 .. kWords - 1 of the
+// final state are live, and the compiler drops the finalisation work that
+// feeds no stored lane: for 64- and 128-bit output, all of the last round's
+// second lane pair and most of the one before.
+template <int kWords>
 __device__ __forceinline__ void store_short_hash(const Batch& b, int64_t m, int bad,
                                                  const State& s) {
   const uint64_t keep = bad ? 0ull : ~0ull;
-  uint64_t* o = b.out + m * b.words;
+  const int words = kWords ? kWords : b.words;
+  uint64_t* o = b.out + m * words;
   o[0] = (s.v0[0] + s.v1[0] + s.mul0[0] + s.mul1[0]) & keep;
-  if (b.words >= 2) o[1] = (s.v0[1] + s.v1[1] + s.mul0[1] + s.mul1[1]) & keep;
-  if (b.words == 4) {
+  if (words >= 2) o[1] = (s.v0[1] + s.v1[1] + s.mul0[1] + s.mul1[1]) & keep;
+  if (words == 4) {
     o[2] = (s.v0[2] + s.v1[2] + s.mul0[2] + s.mul1[2]) & keep;
     o[3] = (s.v0[3] + s.v1[3] + s.mul0[3] + s.mul1[3]) & keep;
   }
@@ -661,8 +666,10 @@ __device__ __forceinline__ void store_short_hash(const Batch& b, int64_t m, int 
 
 // Thread per message for batches whose messages are all at most kShortMax
 // bytes, in index order (neighbouring threads read neighbouring bytes).
-// Three blocks of 256 threads per SM (80 registers).
-template <bool kStream>
+// Three blocks of 256 threads per SM (80 registers).  kWords: the output
+// width in words, fixed per instantiation for whole messages (0 in the
+// stream instantiation, which reads it at run time).
+template <bool kStream, int kWords>
 __global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, const int* run_if) {
   if (run_if != nullptr && *run_if != 0) return;
   resolve_count(b);
@@ -727,7 +734,7 @@ __global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, co
       init(s, key);
       hash_short(s, base + s0, static_cast<uint32_t>(len), base + lo, base + hi);
       finalize(s);
-      store_short_hash(b, m, bad, s);
+      store_short_hash<kWords>(b, m, bad, s);
     }
     return;
   }
@@ -791,7 +798,7 @@ __global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, co
     }
     cur ^= 1;
     finalize(s);
-    store_short_hash(b, m, bad, s);
+    store_short_hash<kWords>(b, m, bad, s);
   }
 }
 
@@ -814,7 +821,10 @@ cudaError_t launch_ragged_t(const Batch& b, const Queue& q, int num_sms, cudaStr
 }  // namespace
 
 cudaError_t launch_short(const Batch& b, const int* run_if, int num_sms, cudaStream_t stream) {
-  auto kern = b.stream_mode != kWholeMessages ? short_kernel<true> : short_kernel<false>;
+  void (*kern)(Batch, const int*) = b.stream_mode != kWholeMessages ? short_kernel<true, 0>
+                                    : b.words == 1                 ? short_kernel<false, 1>
+                                    : b.words == 2                 ? short_kernel<false, 2>
+                                                                   : short_kernel<false, 4>;
   cudaError_t e;
   const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), 256, 0, &e);
   if (e != cudaSuccess) return e;
