@@ -51,8 +51,13 @@ __device__ __forceinline__ uint64_t hash64_upto32(const uint64_t key[4], const u
   return s.v0[0] + s.v1[0] + s.mul0[0] + s.mul1[0];
 }
 
+// kWords output words per counter, fixed per instantiation: the finalisation
+// work that feeds no stored lane (for 64- and 128-bit output, the last
+// round's second lane pair and most of that pair's work in the round before)
+// is dead code the compiler drops.
+template <int kWords>
 __global__ void __launch_bounds__(256) prng_kernel(const uint64_t* key, uint64_t counter0,
-                                                   int64_t n, int words, uint64_t* out) {
+                                                   int64_t n, uint64_t* out) {
   uint64_t k[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) k[i] = __ldg(key + i);
@@ -67,10 +72,10 @@ __global__ void __launch_bounds__(256) prng_kernel(const uint64_t* key, uint64_t
     finalize(s);
     uint64_t h[4];
     digest(s, h);
-    uint64_t* o = out + i * words;
+    uint64_t* o = out + i * kWords;
     o[0] = h[0];
-    if (words >= 2) o[1] = h[1];
-    if (words == 4) {
+    if (kWords >= 2) o[1] = h[1];
+    if (kWords == 4) {
       o[2] = h[2];
       o[3] = h[3];
     }
@@ -181,8 +186,9 @@ int hh_prng_fill(hh_ctx* ctx, int bits, const uint64_t* key, uint64_t counter0, 
   if (key == nullptr || out == nullptr) return HH_ERR_INVALID_ARG;
   hh::DeviceGuard guard(ctx->device);
   if (!guard.ok) return HH_ERR_CUDA;
-  hh::prng_kernel<<<hh::grid_for(n, ctx->num_sms), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      key, counter0, n, words, out);
+  auto kern = words == 1 ? hh::prng_kernel<1> : words == 2 ? hh::prng_kernel<2> : hh::prng_kernel<4>;
+  kern<<<hh::grid_for(n, ctx->num_sms), 256, 0, static_cast<cudaStream_t>(stream)>>>(key, counter0,
+                                                                                    n, out);
   ctx->last_launches = 1;
   return hh::status_of(cudaGetLastError());
 }
