@@ -24,7 +24,6 @@ import re
 import concurrent.futures
 import ctypes
 import gc
-import hashlib
 import json
 import os
 import statistics
@@ -157,22 +156,10 @@ def measured_peak_hbm():
 
 
 def kernel_source_digest(unit: str = "hh_fixed.cu") -> str:
-    """Digest of one kernel translation unit and every csrc header it
-    includes (transitively): the sources the DRAM counters were taken on."""
-    csrc = os.path.join(ROOT, "paper_1612_06257_gb300", "csrc")
-    seen, todo = [], [unit]
-    while todo:
-        f = todo.pop()
-        if f in seen or not os.path.exists(os.path.join(csrc, f)):
-            continue
-        seen.append(f)
-        with open(os.path.join(csrc, f)) as fh:
-            todo += re.findall(r'^#include "([^"]+)"', fh.read(), flags=re.M)
-    h = hashlib.sha256()
-    for f in sorted(seen):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
-    return h.hexdigest()[:16]
+    """Digest of a kernel's translation unit and the csrc headers it
+    includes: the sources the DRAM counters were taken on."""
+    from paper_1612_06257_gb300.build import source_digest
+    return source_digest(unit)
 
 
 def dram_traffic_per_launch(kernel: str):

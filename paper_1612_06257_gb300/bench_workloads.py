@@ -30,7 +30,7 @@ import time
 import numpy as np
 import torch
 
-from paper_1612_06257_gb300 import hh, serve, stats, workloads
+from paper_1612_06257_gb300 import build, hh, serve, stats, workloads
 
 L2_FLUSH_BYTES = 512 << 20
 
@@ -51,6 +51,37 @@ def _max_sm_clock_hz():
             return float(json.load(f)["sm_max_mhz"]) * 1e6
     except (OSError, KeyError, ValueError):
         return 2070e6  # GB300 maximum SM clock
+
+
+def _alu_peak(dev):
+    """ALU-pipe lane-instructions per second: 16 lanes per clock in each of
+    the 4 sub-partitions of every SM, at the maximum SM clock."""
+    props = torch.cuda.get_device_properties(dev)
+    return 16 * 4 * props.multi_processor_count * _max_sm_clock_hz()
+
+
+def _alu_roofline(dev, kernel, unit, source, per_s):
+    """Roofline of an integer-ALU-bound kernel: `per_s` outputs per second
+    against the ALU pipe's lane-instructions per second divided by the ALU
+    lane-instructions one output costs.  That count is ncu's
+    sm__inst_executed_pipe_alu for the kernel on its current sources
+    (profiles/alu_counts.json); None when the sources have changed since."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    try:
+        with open(os.path.join(root, "profiles", "alu_counts.json")) as f:
+            rec = json.load(f)[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    if rec.get("source_digest") != build.source_digest(source):
+        return None
+    per_output = float(rec["alu_lane_instructions_per_output"])
+    peak = _alu_peak(dev) / per_output
+    return {"bound": "alu", "achieved": round(per_s, 1), "peak": round(peak, 1), "unit": unit,
+            "frac": round(per_s / peak, 4), "alu_lane_instructions_per_output": per_output,
+            "kernel": kernel,
+            "peak_source": "derived: 16 ALU lanes/clk per SM sub-partition x 4 x SMs x max SM "
+                           "clock / ALU lane-instructions per output (ncu count, "
+                           "profiles/alu_counts.json)"}
 
 
 def _time(fn, reps, flush=None):
@@ -172,7 +203,9 @@ def short(ctx, dev):
            "updates_per_hash": round(upd_per_hash, 3),
            "integer_ceiling_hashes_per_s": round(ceiling, 1),
            "integer_ceiling": "Update microbenchmark (register state, no memory) measured in "
-                              "this run, divided by the Updates per hash"}
+                              "this run, divided by the Updates per hash; whole Updates are "
+                              "counted, although for 64- and 128-bit output the finalisation "
+                              "work that feeds no stored lane is not computed"}
     for bits, fn in ((64, hh.hh_hash64_batch), (128, hh.hh_hash128_batch)):
         out = torch.empty(w.n * bits // 64, dtype=torch.int64, device=dev)
         ms, _ = _time(lambda: fn(ctx, w.keys, 0, w.data, w.offsets, out=out), 10)
@@ -181,6 +214,8 @@ def short(ctx, dev):
         res["integer_frac_%d" % bits] = round(hps / ceiling, 4)
         res["launches_per_batch_%d" % bits] = hh.hh_last_launch_count(ctx)
         res["gbps_%d" % bits] = round(w.total_bytes / ms / 1e6, 1)
+        res["alu_roofline_%d" % bits] = _alu_roofline(
+            dev, "short_kernel<false,%d>" % (bits // 64), "hashes/s", "hh_ragged.cu", hps)
         if bits == 64:
             naive = _naive_ms(ctx, lambda: fn(ctx, w.keys, 0, w.data, w.offsets, out=out), 5)
             res["naive_hashes_per_s_64"] = round(w.n / (naive / 1e3), 1)
@@ -251,9 +286,8 @@ def siptree(ctx, dev, w=None):
     # = L / 32 vectors: 4 P (24 c + 4) for the lanes, 4 (24 (c + d) + 4) for
     # their last word and finalisation, and (6 c + d) 24 + 28 for the fold.
     # The ALU pipe retires 16 lanes per clock per SM sub-partition.
-    props = torch.cuda.get_device_properties(dev)
     sm_hz = _max_sm_clock_hz()
-    alu_peak = 16 * 4 * props.multi_processor_count * sm_hz  # ALU lane-instructions per second
+    alu_peak = _alu_peak(dev)  # ALU lane-instructions per second
     length = w.fixed_len or int(w.total_bytes // max(1, w.n))
     vectors = (length + 31) // 32
     for name, (c, d) in (("siptree", (2, 4)), ("siptree13", (1, 3))):
@@ -279,11 +313,14 @@ def prng(ctx, dev):
     key = workloads.random_u64((4,), workloads.generator(9, dev), dev)
     out = torch.empty(n, dtype=torch.int64, device=dev)
     ms, _ = _time(lambda: hh.hh_prng_fill(ctx, 64, key, 12345, n, out=out), 10)
-    ceiling = _update_ceiling(ctx, dev) / 5.0
     wps = n / (ms / 1e3)
     return {"workload": "2^28 words, 64-bit, counter-mode (8-byte counters)",
             "ms": round(ms, 3), "words_per_s": round(wps, 1), "gbps_out": round(n * 8 / ms / 1e6, 1),
-            "integer_ceiling_words_per_s": round(ceiling, 1), "integer_frac": round(wps / ceiling, 4)}
+            "updates_per_word": 5,
+            "alu_roofline": _alu_roofline(dev, "prng_kernel<1>", "words/s", "hh_stats.cu", wps),
+            "note": "for 64-bit output the finalisation work that feeds no stored lane is not "
+                    "computed, so a word costs fewer ALU instructions than five whole Updates "
+                    "(the Update microbenchmark's rate / 5 is not a ceiling here)"}
 
 
 def stats_study(ctx, dev):

@@ -6,7 +6,9 @@ then nvcc links them into paper_1612_06257_gb300/libhh.so.  No cmake.
 from __future__ import annotations
 
 import concurrent.futures
+import hashlib
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -28,6 +30,24 @@ def nvcc() -> str:
         if cand and os.path.exists(cand):
             return cand
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libhh")
+
+
+def source_digest(unit: str) -> str:
+    """Digest of one CUDA translation unit under csrc/ and every csrc header
+    it includes (transitively): the sources a profiler count was taken on."""
+    seen, todo = [], [unit]
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.exists(os.path.join(CSRC, f)):
+            continue
+        seen.append(f)
+        with open(os.path.join(CSRC, f)) as fh:
+            todo += re.findall(r'^#include "([^"]+)"', fh.read(), flags=re.M)
+    h = hashlib.sha256()
+    for f in sorted(seen):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
 
 
 def sources() -> list[str]:

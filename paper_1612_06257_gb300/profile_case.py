@@ -7,8 +7,9 @@ ABI (the first launch warms up; profile with `-s 1 -c 1` to capture the
 second).  Kinds: fixed (hh_hash_fixed), ragged (log-uniform lengths,
 per-message keys), short (0..64-byte messages), long (n messages of
 `--length` bytes through the offsets form: solo or pair tiles from 128 KiB)
-and siptree (n messages of `--length` bytes, SipTreeHash through
-hh_siptree_batch; --bits 13 for SipTreeHash13).
+siptree (n messages of `--length` bytes, SipTreeHash through
+hh_siptree_batch; --bits 13 for SipTreeHash13) and prng (n counters of
+counter mode through hh_prng_fill, --bits of output each).
 """
 import argparse
 
@@ -19,7 +20,7 @@ from paper_1612_06257_gb300 import hh, workloads
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("--kind", choices=["fixed", "ragged", "short", "long", "siptree"],
+    p.add_argument("--kind", choices=["fixed", "ragged", "short", "long", "siptree", "prng"],
                    default="fixed")
     p.add_argument("--n", type=int, default=1 << 18)
     p.add_argument("--length", type=int, default=1024)
@@ -30,6 +31,16 @@ def main():
     ctx = hh.hh_init(0)
     hh.hh_set_kernel(ctx, a.kernel)
     dev = "cuda:0"
+    if a.kind == "prng":
+        # n counters of counter mode (8-byte little-endian counters), a.bits
+        # of output each
+        key = workloads.random_u64((4,), workloads.generator(1, dev), dev)
+        out = torch.empty(a.n * a.bits // 64, dtype=torch.int64, device=dev)
+        for _ in range(a.reps):
+            hh.hh_prng_fill(ctx, a.bits, key, 12345, a.n, out=out)
+        torch.cuda.synchronize()
+        print("ok", a.kind, a.n, a.bits)
+        return
     if a.kind == "fixed":
         w = workloads.fixed(a.n, a.length, seed=1, device=dev)
     elif a.kind == "ragged":
