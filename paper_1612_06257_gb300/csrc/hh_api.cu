@@ -132,6 +132,7 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
     q.solo_shared = ctx->tune.solo_shared;
     q.tiles = std::max((n + 31) / 32, std::min(n, q.solo_max));
     e = hh::launch_ragged(b, q, ctx->tune.ragged, ctx->num_sms, stream);
+    if (q.skip_if_short) ctx->last_launches += 1;  // two warp-tile variants, one runs
   }
   ctx->last_launches += 1;
   return to_status(e);
