@@ -60,21 +60,32 @@ def _alu_peak(dev):
     return 16 * 4 * props.multi_processor_count * _max_sm_clock_hz()
 
 
-def _alu_roofline(dev, kernel, unit, source, per_s):
-    """Roofline of an integer-ALU-bound kernel: `per_s` outputs per second
-    against the ALU pipe's lane-instructions per second divided by the ALU
-    lane-instructions one output costs.  That count is ncu's
-    sm__inst_executed_pipe_alu for the kernel on its current sources
-    (profiles/alu_counts.json); None when the sources have changed since."""
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+def _alu_count(kernel, source, path=None):
+    """ALU lane-instructions per output of `kernel`: ncu's
+    sm__inst_executed_pipe_alu on the kernel's sources, as committed in
+    profiles/alu_counts.json; None when there is no count or the sources
+    (translation unit `source` and its csrc headers) changed since."""
+    if path is None:
+        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        path = os.path.join(root, "profiles", "alu_counts.json")
     try:
-        with open(os.path.join(root, "profiles", "alu_counts.json")) as f:
+        with open(path) as f:
             rec = json.load(f)[kernel]
     except (OSError, KeyError, ValueError):
         return None
     if rec.get("source_digest") != build.source_digest(source):
         return None
-    per_output = float(rec["alu_lane_instructions_per_output"])
+    return float(rec["alu_lane_instructions_per_output"])
+
+
+def _alu_roofline(dev, kernel, unit, source, per_s):
+    """Roofline of an integer-ALU-bound kernel: `per_s` outputs per second
+    against the ALU pipe's lane-instructions per second divided by the ALU
+    lane-instructions one output costs (_alu_count); None without a count
+    for the current sources."""
+    per_output = _alu_count(kernel, source)
+    if per_output is None:
+        return None
     peak = _alu_peak(dev) / per_output
     return {"bound": "alu", "achieved": round(per_s, 1), "peak": round(peak, 1), "unit": unit,
             "frac": round(per_s / peak, 4), "alu_lane_instructions_per_output": per_output,

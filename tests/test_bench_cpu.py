@@ -31,3 +31,36 @@ def test_both_arms_measure_the_same_workload():
     assert "N_MESSAGES, MESSAGE_BYTES, seed=1000 + rank" in ours_src
     cfg = bench.workload_config()
     assert cfg["n_messages"] == 1 << 20 and cfg["message_bytes"] == 1024
+
+
+def test_committed_profiler_counts_match_the_kernel_sources():
+    """profiles/traffic.json and profiles/alu_counts.json were taken on the
+    kernels as committed: their source digests match the current translation
+    units (the bench leaves a figure out once they do not)."""
+    import json
+    import os
+    import bench
+    from paper_1612_06257_gb300.build import source_digest
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    traffic = json.load(open(os.path.join(root, "profiles", "traffic.json")))
+    assert traffic["fixed_tma_kernel<128,2,2>"]["source_digest"] == bench.kernel_source_digest()
+    counts = json.load(open(os.path.join(root, "profiles", "alu_counts.json")))
+    assert {"short_kernel<false,1>", "short_kernel<false,2>", "prng_kernel<1>"} <= set(counts)
+    for name, rec in counts.items():
+        assert rec["source_digest"] == source_digest(rec["source_unit"]), name
+        assert rec["alu_lane_instructions_per_output"] > 0 and "ncu" in rec["command"]
+
+
+def test_alu_count_needs_a_matching_digest(tmp_path):
+    import json
+    from paper_1612_06257_gb300 import bench_workloads as bw
+    from paper_1612_06257_gb300.build import source_digest
+    path = tmp_path / "counts.json"
+    good = {"source_digest": source_digest("hh_stats.cu"), "alu_lane_instructions_per_output": 7.5}
+    stale = dict(good, source_digest="0" * 16)
+    path.write_text(json.dumps({"k": good, "old": stale}))
+    assert bw._alu_count("k", "hh_stats.cu", str(path)) == 7.5
+    assert bw._alu_count("old", "hh_stats.cu", str(path)) is None
+    assert bw._alu_count("k", "hh_ragged.cu", str(path)) is None  # another unit's digest
+    assert bw._alu_count("missing", "hh_stats.cu", str(path)) is None
+    assert bw._alu_count("k", "hh_stats.cu", str(tmp_path / "absent.json")) is None
