@@ -107,9 +107,10 @@ def test_ragged_loguniform_small(ctx):
     assert np.array_equal(run_ragged(ctx, w, 64, "unsorted"), expect)
 
 
-@pytest.mark.parametrize("bits", [64, 128])
+@pytest.mark.parametrize("bits", [64, 128, 256])
 def test_short_messages_small(ctx, bits):
-    """Lengths uniform in [0, 64], 10% all-zero messages, one key; n = 65536."""
+    """Lengths uniform in [0, 64], 10% all-zero messages, one key; n = 65536
+    (the short kernel, one instantiation per output width)."""
     w = workloads.short(65536, seed=7, device=DEV)
     assert np.array_equal(run_ragged(ctx, w, bits), oracle_hashes(w, bits))
 
@@ -188,7 +189,7 @@ def test_short_kernel_at_unaligned_batch_ends(ctx, per_message_keys):
     backing[3:3 + w.total_bytes] = w.data
     view = backing[3:3 + w.total_bytes]
     shifted = workloads.Workload("short", view, w.offsets, None, w.keys, per_message_keys, w.n)
-    for bits in (64, 128):
+    for bits in (64, 128, 256):
         assert np.array_equal(run_ragged(ctx, shifted, bits), oracle_hashes(w, bits))
 
 
