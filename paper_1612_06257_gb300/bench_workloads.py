@@ -291,25 +291,35 @@ def siptree(ctx, dev, w=None):
         ms, _ = _time(fn, 10)
         res["%s_gbps" % name] = round(w.total_bytes / ms / 1e6, 1)
         res["%s_ms" % name] = round(ms, 4)
-    # Integer-ALU roofline: a SipRound is 24 ALU instructions (4 64-bit adds,
-    # 4 rotations of two funnel shifts, 4 64-bit xors; the 32-bit rotations
-    # are free) and a compression adds 4 xors.  Per message of L bytes with P
-    # = L / 32 vectors: 4 P (24 c + 4) for the lanes, 4 (24 (c + d) + 4) for
-    # their last word and finalisation, and (6 c + d) 24 + 28 for the fold.
-    # The ALU pipe retires 16 lanes per clock per SM sub-partition.
+    # Integer-ALU roofline: the ALU pipe's lane-instructions per second over
+    # the ALU lane-instructions one 1 KiB message costs, as ncu counts them on
+    # the kernel's current sources (profiles/alu_counts.json; no roofline for
+    # other lengths or once the sources have changed).  The hand count beside
+    # it: a SipRound is 24 ALU instructions (4 64-bit adds, 4 rotations of two
+    # funnel shifts, 4 64-bit xors; the 32-bit rotations are free) and a
+    # compression adds 4 xors, so a message of P = L / 32 vectors takes
+    # 4 P (24 c + 4) for the lanes, 4 (24 (c + d) + 4) for their last word and
+    # finalisation, and (6 c + d) 24 + 28 for the fold; the compiler needs fewer.
     sm_hz = _max_sm_clock_hz()
     alu_peak = _alu_peak(dev)  # ALU lane-instructions per second
     length = w.fixed_len or int(w.total_bytes // max(1, w.n))
     vectors = (length + 31) // 32
-    for name, (c, d) in (("siptree", (2, 4)), ("siptree13", (1, 3))):
-        alu = 4 * vectors * (24 * c + 4) + 4 * (24 * (c + d) + 4) + (6 * c + d) * 24 + 28
+    for name, kernel, (c, d) in (("siptree", "siptree_kernel<2,4>", (2, 4)),
+                                 ("siptree13", "siptree_kernel<1,3>", (1, 3))):
+        hand = 4 * vectors * (24 * c + 4) + 4 * (24 * (c + d) + 4) + (6 * c + d) * 24 + 28
+        alu = _alu_count(kernel, "hh_siptree.cu") if length == 1024 else None
+        if alu is None:
+            res["%s_roofline" % name] = None
+            continue
         ceiling = alu_peak / alu * length / 1e9  # GB/s of payload
         res["%s_roofline" % name] = {
             "bound": "alu", "achieved": res["%s_gbps" % name], "peak": round(ceiling, 1),
             "unit": "GB/s", "frac": round(res["%s_gbps" % name] / ceiling, 4),
-            "alu_instructions_per_message": alu, "sm_clock_hz": sm_hz,
-            "peak_source": "derived: 16 ALU lanes/clk per SM sub-partition x 4 x SMs x "
-                           "max SM clock / ALU instructions per message"}
+            "alu_lane_instructions_per_message": alu, "alu_hand_count_per_message": hand,
+            "sm_clock_hz": sm_hz, "kernel": kernel,
+            "peak_source": "derived: 16 ALU lanes/clk per SM sub-partition x 4 x SMs x max SM "
+                           "clock / ALU lane-instructions per message (ncu count, "
+                           "profiles/alu_counts.json)"}
     res["highwayhash_over_siptree"] = round(res["highwayhash_gbps"] / res["siptree_gbps"], 2)
     res["highwayhash_over_siptree13"] = round(res["highwayhash_gbps"] / res["siptree13_gbps"], 2)
     # Table 1 at 1024 B (cycles per byte on one Haswell core): SipTreeHash
