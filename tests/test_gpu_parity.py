@@ -442,6 +442,27 @@ def test_huge_messages_run_in_solo_and_pair_tiles(huge_ctx):
         assert np.array_equal(got, run_ragged(ctx, w, bits, "unsorted"))
 
 
+def test_large_batch_with_huge_messages(huge_ctx):
+    """Above 8192 messages the sort runs in three launches and both variants
+    of the warp-tile kernel are launched (with and without the huge-message
+    phase); with huge messages present the variant with the phase does all
+    the work.  20000 ordinary messages and six of 128 KiB to 1 MiB + 13,
+    unaligned starts, against the oracle."""
+    ctx = huge_ctx
+    g = torch.Generator().manual_seed(93)
+    lengths = torch.cat([torch.randint(0, 5000, (20000,), generator=g),
+                         torch.tensor([1 << 17, (1 << 17) + 1, 300001, 500000, 777777,
+                                       (1 << 20) + 13])])
+    lengths = lengths[torch.randperm(lengths.numel(), generator=g)]
+    w = workloads.from_lengths(lengths, seed=93, device=DEV, per_message_keys=True)
+    big = np.nonzero(lengths.numpy() >= (1 << 17))[0]
+    idx = np.unique(np.concatenate([big, np.arange(0, w.n, 13), [w.n - 1]]))
+    for bits in (64, 256):
+        got = run_ragged(ctx, w, bits)
+        assert hh.hh_last_launch_count(ctx) == 6  # sort 3, short kernel 1, warp tiles 2
+        assert np.array_equal(got[idx], oracle_hashes(w, bits, indices=idx)), bits
+
+
 def test_single_huge_message_alone(huge_ctx):
     """A batch of one message (sorted too): 2 MiB + 17 bytes starting at an
     odd offset of its buffer, and one ending on the buffer's last byte."""
