@@ -226,7 +226,7 @@ def short(ctx, dev):
         res["launches_per_batch_%d" % bits] = hh.hh_last_launch_count(ctx)
         res["gbps_%d" % bits] = round(w.total_bytes / ms / 1e6, 1)
         res["alu_roofline_%d" % bits] = _alu_roofline(
-            dev, "short_kernel<false,%d>" % (bits // 64), "hashes/s", "hh_ragged.cu", hps)
+            dev, "short_count_kernel<%d>" % (bits // 64), "hashes/s", "hh_ragged.cu", hps)
         if bits == 64:
             naive = _naive_ms(ctx, lambda: fn(ctx, w.keys, 0, w.data, w.offsets, out=out), 5)
             res["naive_hashes_per_s_64"] = round(w.n / (naive / 1e3), 1)

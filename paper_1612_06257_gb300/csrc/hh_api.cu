@@ -14,6 +14,7 @@
 
 #include "hh.h"
 #include "hh_context.h"
+#include "hh_count.h"
 #include "hh_internal.h"
 
 namespace {
@@ -89,14 +90,29 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
   }
 
   const bool sort = !fixed && ctx->kernel != HH_KERNEL_STAGED_UNSORTED && n >= kSortMinMessages;
+  const bool with_short = sort && ctx->kernel != HH_KERNEL_STAGED_BULK && n > kShortKernelMinMessages;
+  // One-key offsets-form batches count their lengths inside the short
+  // kernel (hh_count.h): one pass over the offsets fewer.
+  const bool counted_short = with_short && hh::short_count_eligible(b);
   hh::Queue q{};
   if (sort) {
     // The batch must fit the scratch reserved by hh_init / hh_reserve.
     if (n > ctx->perm_cap) return HH_ERR_TOO_LARGE;
     int launches = 0;
-    cudaError_t e = hh::launch_bucket_sort(b, ctx->d_hist, ctx->d_cursor, ctx->d_perm,
+    cudaError_t e;
+    if (counted_short) {
+      e = cudaMemsetAsync(ctx->d_hist, 0, sizeof(uint32_t) * (hh::kBuckets + 1), stream);
+      if (e == cudaSuccess) e = hh::launch_short_counted(b, ctx->d_hist, ctx->num_sms, stream);
+      if (e == cudaSuccess)
+        e = hh::launch_bucket_scan_scatter(b, ctx->d_hist, ctx->d_cursor, ctx->d_perm,
                                            ctx->d_next_tile, ctx->d_use_perm, ctx->d_huge,
                                            ctx->tune.huge_bucket, ctx->num_sms, stream, &launches);
+      launches += 1;
+    } else {
+      e = hh::launch_bucket_sort(b, ctx->d_hist, ctx->d_cursor, ctx->d_perm, ctx->d_next_tile,
+                                 ctx->d_use_perm, ctx->d_huge, ctx->tune.huge_bucket,
+                                 ctx->num_sms, stream, &launches);
+    }
     ctx->last_launches += launches;
     if (e != cudaSuccess) return to_status(e);
     q.perm = ctx->d_perm;
@@ -112,16 +128,19 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
                            (b.fixed_len % 16 == 0);
     e = hh::launch_staged(b, q, ctx->shape_bulk, aligned16, ctx->num_sms, stream);
   } else {
-    if (sort && n > kShortKernelMinMessages) {
+    if (with_short) {
       // All-short batches (the sort's flag says no message is longer than
       // kShortMax) run in the short kernel; otherwise it returns at once and
       // the warp-tile kernel runs.  Both are enqueued, so the sequence of
       // launches does not depend on the data.  Small batches skip the short
       // kernel: the warp-tile kernel hashes all-short tiles without shared
-      // memory too, and one launch fewer matters more there.
-      e = hh::launch_short(b, ctx->d_use_perm, ctx->num_sms, stream);
-      if (e != cudaSuccess) return to_status(e);
-      ctx->last_launches += 1;
+      // memory too, and one launch fewer matters more there.  (With the
+      // count inside the short kernel, it ran before the sort's scan.)
+      if (!counted_short) {
+        e = hh::launch_short(b, ctx->d_use_perm, ctx->num_sms, stream);
+        if (e != cudaSuccess) return to_status(e);
+        ctx->last_launches += 1;
+      }
       q.skip_if_short = 1;
     }
     // The grid is sized for warp tiles of 32, or for up to solo_max solo
@@ -260,7 +279,7 @@ int hh_init(hh_ctx** out, int device, const char* tune_cache_path) {
             cudaMalloc(&ctx->d_next_tile, 4 * sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&ctx->d_use_perm, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&ctx->d_huge, sizeof(long long)) == cudaSuccess &&
-            cudaMalloc(&ctx->d_hist, sizeof(uint32_t) * hh::kBuckets) == cudaSuccess &&
+            cudaMalloc(&ctx->d_hist, sizeof(uint32_t) * (hh::kBuckets + 1)) == cudaSuccess &&
             cudaMalloc(&ctx->d_cursor, sizeof(uint32_t) * hh::kBuckets) == cudaSuccess &&
             cudaMemset(ctx->d_err, 0, sizeof(int)) == cudaSuccess &&
             cudaMemset(ctx->d_next_tile, 0, 4 * sizeof(unsigned long long)) == cudaSuccess &&

@@ -11,7 +11,8 @@
 // kHugeBucket, 128 KiB), which the hash kernel runs two threads per message.
 //
 // Three kernels: per-block histograms merged with one global atomic per
-// non-empty bucket; a one-block exclusive scan in descending bucket order
+// non-empty bucket (for one-key offsets-form batches above 8192 messages
+// this count runs inside the short kernel instead: hh_count.h); a one-block exclusive scan in descending bucket order
 // (which also resets the tile counter of the work queue); and a scatter that
 // ranks elements inside each 8192-element chunk in shared memory and reserves
 // each bucket's range with one global atomic per chunk.  A batch of at most
@@ -23,6 +24,7 @@
 #include <cstdint>
 
 #include "hh_batch.cuh"
+#include "hh_count.h"
 #include "hh_internal.h"
 
 namespace hh {
@@ -194,11 +196,20 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scan_kernel(const uint32_
 
 // Ranks of chunk elements c .. c + kChunk - 1 inside their buckets: counts
 // into cnt[] (shared, zeroed by the caller) and returns each element's key
-// (-1 past the end) and rank.
+// (-1 past the end) and rank.  kMergeShort: buckets 0..2 (messages of at
+// most kShortMax bytes) are one bucket, 2, as the count inside the short
+// kernel makes them.
+template <bool kMergeShort>
 __device__ __forceinline__ void rank_chunk(const Batch& b, int64_t n, int64_t c, uint32_t* cnt,
                                            int key[kPerThread], uint32_t rank[kPerThread]) {
   const int lane = threadIdx.x & 31;
   bucket_keys(b, n, c, key);
+  if (kMergeShort) {
+    constexpr int kShortBucket = kShortMax / 32;
+#pragma unroll
+    for (int e = 0; e < kPerThread; ++e)
+      key[e] = key[e] >= 0 && key[e] < kShortBucket ? kShortBucket : key[e];
+  }
 #pragma unroll
   for (int e = 0; e < kPerThread; ++e) {
     const unsigned peers = __match_any_sync(0xffffffffu, key[e]);
@@ -223,7 +234,7 @@ __global__ void __launch_bounds__(kSortThreads) bucket_small_kernel(
   __syncthreads();
   int key[kPerThread];
   uint32_t rank[kPerThread];
-  rank_chunk(b, n, 0, cnt, key, rank);
+  rank_chunk<false>(b, n, 0, cnt, key, rank);
   __syncthreads();
   if (!scan_descending(cnt, base, next_tile, use_perm, huge_count, huge_bucket)) return;
 #pragma unroll
@@ -233,6 +244,7 @@ __global__ void __launch_bounds__(kSortThreads) bucket_small_kernel(
   }
 }
 
+template <bool kMergeShort>
 __global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(Batch b, uint32_t* cursor,
                                                                       int32_t* perm,
                                                                       const int* use_perm) {
@@ -247,7 +259,7 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(Batch b, u
     __syncthreads();
     int key[kPerThread];
     uint32_t rank[kPerThread];
-    rank_chunk(b, n, c, cnt, key, rank);
+    rank_chunk<kMergeShort>(b, n, c, cnt, key, rank);
     __syncthreads();
     for (int i = threadIdx.x; i < kBuckets; i += kSortThreads)
       if (cnt[i]) base[i] = atomicAdd(&cursor[i], cnt[i]);
@@ -263,6 +275,29 @@ __global__ void __launch_bounds__(kSortThreads) bucket_scatter_kernel(Batch b, u
 
 }  // namespace
 
+namespace {
+
+int sort_grid(int64_t n, int num_sms) {
+  const int64_t chunks = (n + kChunk - 1) / kChunk;
+  const int64_t cap = static_cast<int64_t>(num_sms) * 2;
+  return static_cast<int>(chunks < cap ? chunks : cap);
+}
+
+}  // namespace
+
+cudaError_t launch_bucket_scan_scatter(const Batch& b, uint32_t* hist, uint32_t* cursor,
+                                       int32_t* perm, unsigned long long* next_tile,
+                                       int* use_perm, long long* huge_count, int huge_bucket,
+                                       int num_sms, cudaStream_t stream, int* launches) {
+  bucket_scan_kernel<<<1, kSortThreads, 0, stream>>>(hist, cursor, next_tile, use_perm,
+                                                      huge_count, huge_bucket);
+  const int grid = sort_grid(b.n, num_sms);
+  if (grid > 0)
+    bucket_scatter_kernel<true><<<grid, kSortThreads, 0, stream>>>(b, cursor, perm, use_perm);
+  *launches += grid > 0 ? 2 : 1;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bucket_sort(const Batch& b, uint32_t* hist,
                                uint32_t* cursor, int32_t* perm, unsigned long long* next_tile,
                                int* use_perm, long long* huge_count, int huge_bucket,
@@ -276,13 +311,11 @@ cudaError_t launch_bucket_sort(const Batch& b, uint32_t* hist,
   }
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kBuckets, stream);
   if (e != cudaSuccess) return e;
-  const int64_t chunks = (n + kChunk - 1) / kChunk;
-  const int64_t cap = static_cast<int64_t>(num_sms) * 2;
-  const int grid = static_cast<int>(chunks < cap ? chunks : cap);
+  const int grid = sort_grid(n, num_sms);
   bucket_count_kernel<<<grid, kSortThreads, 0, stream>>>(b, hist);
   bucket_scan_kernel<<<1, kSortThreads, 0, stream>>>(hist, cursor, next_tile, use_perm,
                                                       huge_count, huge_bucket);
-  bucket_scatter_kernel<<<grid, kSortThreads, 0, stream>>>(b, cursor, perm, use_perm);
+  bucket_scatter_kernel<false><<<grid, kSortThreads, 0, stream>>>(b, cursor, perm, use_perm);
   *launches += 3;
   return cudaGetLastError();
 }

@@ -20,12 +20,14 @@
 // the shared-memory banks.
 //
 // Batches of messages of at most 64 bytes run in short_kernel instead (one
-// thread per message, pipelined through shared memory).
+// thread per message, pipelined through shared memory); for large one-key
+// batches short_count_kernel, which also counts the length sort's buckets.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "hh_batch.cuh"
+#include "hh_count.h"
 #include "hh_device.cuh"
 #include "hh_internal.h"
 #include "hh_ptx.cuh"
@@ -809,6 +811,176 @@ __global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, co
   }
 }
 
+// The flag that some message is longer than kShortMax: relaxed GPU-scope
+// accesses, so that a store on one SM reaches the loads of the others.
+__device__ __forceinline__ uint32_t load_flag(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ void set_flag(uint32_t* p) {
+  asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(1u) : "memory");
+}
+
+// short_kernel's one-key offsets-form loop with the length count of the
+// sort folded in (one pass over the offsets instead of two).  The count
+// merges buckets 0..2 (messages of at most kShortMax bytes, whose order
+// among themselves does not matter) into bucket 2, as the scatter of this
+// path does: a message longer than kShortMax goes to its own bucket
+// (bucket_of_packets of ceil(len / 32)), and bucket 2 gets the others.  The
+// block's histogram reuses the staged-word buffer once every thread of the
+// block has left the hash loop (no copy is then in flight), so the kernel
+// takes no more shared memory, and L1 no less, than short_kernel.
+// A message of at most kShortMax bytes is hashed, until the thread meets a
+// longer one or finds the flag hist[kBuckets] that a thread which met one
+// has set; from then on the thread only counts (four messages per step, the
+// offsets loaded together).  So the hash loop counts nothing.  A set flag
+// means a long message is in the histogram: the scan turns the sorted order
+// on and the warp-tile kernel hashes every message, so none skipped here
+// goes unhashed.  In an all-short batch nothing sets the flag and every
+// message is hashed here.
+template <int kWords>
+__global__ void __launch_bounds__(256, 3) short_count_kernel(Batch b, uint32_t* hist) {
+  const int64_t n = b.n;
+  int64_t lo, hi;
+  batch_range(b, lo, hi);
+  const uintptr_t base = reinterpret_cast<uintptr_t>(b.bytes);
+  uint32_t* flag = hist + kBuckets;
+  __shared__ int64_t next_offsets[2][256][2];
+  __shared__ uint32_t next_words[2][256 * 17];
+  __shared__ __align__(16) uint64_t s_init[16];
+  static_assert(sizeof(next_words) >= kBuckets * sizeof(uint32_t), "histogram space");
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    uint64_t key[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) key[i] = __ldg(b.keys + i);
+    State s0;
+    init(s0, key);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      s_init[i] = s0.v0[i];
+      s_init[4 + i] = s0.v1[i];
+      s_init[8 + i] = s0.mul0[i];
+      s_init[12 + i] = s0.mul1[i];
+    }
+  }
+  __syncthreads();
+  auto fetch_offsets = [&](int64_t mm, int slot) {
+    cp_async8(smem_u32(&next_offsets[slot][tid][0]), b.offsets + mm);
+    cp_async8(smem_u32(&next_offsets[slot][tid][1]), b.offsets + mm + 1);
+    cp_async_commit();
+  };
+  auto fetch_words = [&](int slot) {  // the slot's offsets have landed
+    const int64_t s = next_offsets[slot][tid][0], e = next_offsets[slot][tid][1];
+    const int64_t l = e < s ? 0 : e - s;
+    if (l > kShortMax) return;  // only counted
+    uint32_t* dst = &next_words[slot][17 * tid];
+    stage_short_words(dst, smem_u32(dst), base + s, static_cast<uint32_t>(l), base + lo, base + hi);
+  };
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * 256;
+  const int64_t first_m = static_cast<int64_t>(blockIdx.x) * 256 + tid;
+  int64_t m = first_m;
+  if (m < n) {
+    fetch_offsets(m, 0);
+    cp_async_wait<0>();
+    fetch_words(0);
+  }
+  int cur = 0;
+  uint32_t seen = 0;
+  for (; m < n; m += stride) {
+    cp_async_wait<0>();  // this message's offsets and words are in slot cur
+    const int64_t s0 = next_offsets[cur][tid][0], e0 = next_offsets[cur][tid][1];
+    const int bad = e0 < s0 ? kErrBadOffsets : 0;
+    const int64_t len = bad ? 0 : e0 - s0;
+    if (len > kShortMax || seen != 0) break;  // m is counted below
+    const bool more = m + stride < n;
+    if (more) fetch_offsets(m + stride, cur ^ 1);
+    seen = load_flag(flag);
+    if (bad) record_error(b.err, bad);
+    State s;
+    {
+      const uint4* p = reinterpret_cast<const uint4*>(s_init);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const uint4 a = p[i], c = p[2 + i], d = p[4 + i], e = p[6 + i];
+        s.v0[2 * i] = join(a.x, a.y);
+        s.v0[2 * i + 1] = join(a.z, a.w);
+        s.v1[2 * i] = join(c.x, c.y);
+        s.v1[2 * i + 1] = join(c.z, c.w);
+        s.mul0[2 * i] = join(d.x, d.y);
+        s.mul0[2 * i + 1] = join(d.z, d.w);
+        s.mul1[2 * i] = join(e.x, e.y);
+        s.mul1[2 * i + 1] = join(e.z, e.w);
+      }
+    }
+    hash_short_slot(s, &next_words[cur][17 * tid], static_cast<uint32_t>((base + s0) & 3),
+                    static_cast<uint32_t>(len));
+    if (more) {
+      cp_async_wait<0>();
+      fetch_words(cur ^ 1);
+    }
+    cur ^= 1;
+    finalize(s);
+    store_short_hash<kWords>(b, m, bad, s);
+  }
+  // Count only, from message m on: the long ones, runs of equal buckets
+  // with one shared atomic per run.  The barrier waits for the block's
+  // threads to leave the hash loop (each waited for its own copies there).
+  __syncthreads();
+  uint32_t* h = &next_words[0][0];
+  for (int i = tid; i < kBuckets; i += 256) h[i] = 0;
+  __syncthreads();
+  uint32_t big = 0;
+  int run_key = 0;
+  uint32_t run = 0;
+  bool told = false;
+  for (; m < n; m += 4 * stride) {
+    int64_t st[4], en[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = m + k * stride;
+      const int64_t j = i < n ? i : n - 1;
+      st[k] = __ldg(b.offsets + j);
+      en[k] = __ldg(b.offsets + j + 1);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (m + k * stride < n) {
+        const int64_t len = en[k] - st[k];
+        if (len > kShortMax) {
+          const int key = bucket_of_packets((len + 31) >> 5);
+          if (!told) {
+            set_flag(flag);
+            told = true;
+          }
+          ++big;
+          if (key != run_key) {
+            if (run != 0) atomicAdd(&h[run_key], run);
+            run_key = key;
+            run = 0;
+          }
+          ++run;
+        }
+      }
+    }
+  }
+  if (run != 0) atomicAdd(&h[run_key], run);
+  // Bucket 2: the thread's messages that are not long, one shared atomic
+  // per warp; then the block's histogram goes to hist, one global atomic
+  // per non-empty bucket.
+  const uint32_t mine =
+      first_m < n ? static_cast<uint32_t>((n - 1 - first_m) / stride + 1) : 0u;
+  uint32_t short_count = mine - big;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) short_count += __shfl_xor_sync(0xffffffffu, short_count, d);
+  if ((tid & 31) == 0 && short_count != 0) atomicAdd(&h[2], short_count);
+  __syncthreads();
+  for (int i = tid; i < kBuckets; i += 256)
+    if (h[i] != 0) atomicAdd(&hist[i], h[i]);
+}
+
 template <int W, int NST, int WARPS, bool kHuge>
 cudaError_t launch_ragged_v(const Batch& b, const Queue& q, int num_sms, cudaStream_t stream) {
   using L = RaggedLayout<W, NST>;
@@ -852,6 +1024,22 @@ cudaError_t launch_short(const Batch& b, const int* run_if, int num_sms, cudaStr
   const int grid = static_cast<int>(blocks < cap ? blocks : cap);
   if (grid <= 0) return cudaSuccess;
   kern<<<grid, 256, 0, stream>>>(b, run_if);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_short_counted(const Batch& b, uint32_t* hist, int num_sms,
+                                 cudaStream_t stream) {
+  void (*kern)(Batch, uint32_t*) = b.words == 1   ? short_count_kernel<1>
+                                   : b.words == 2 ? short_count_kernel<2>
+                                                  : short_count_kernel<4>;
+  cudaError_t e;
+  const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), 256, 0, &e);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (b.n + 255) / 256;
+  const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
+  const int grid = static_cast<int>(blocks < cap ? blocks : cap);
+  if (grid <= 0) return cudaSuccess;
+  kern<<<grid, 256, 0, stream>>>(b, hist);
   return cudaGetLastError();
 }
 

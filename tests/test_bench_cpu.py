@@ -45,7 +45,7 @@ def test_committed_profiler_counts_match_the_kernel_sources():
     traffic = json.load(open(os.path.join(root, "profiles", "traffic.json")))
     assert traffic["fixed_tma_kernel<128,2,2>"]["source_digest"] == bench.kernel_source_digest()
     counts = json.load(open(os.path.join(root, "profiles", "alu_counts.json")))
-    assert {"short_kernel<false,1>", "short_kernel<false,2>", "prng_kernel<1>",
+    assert {"short_count_kernel<1>", "short_count_kernel<2>", "prng_kernel<1>",
             "siptree_kernel<2,4>", "siptree_kernel<1,3>"} <= set(counts)
     for name, rec in counts.items():
         assert rec["source_digest"] == source_digest(rec["source_unit"]), name

@@ -242,6 +242,39 @@ def test_short_kernel_offsets_that_jump_back(ctx):
     assert np.array_equal(got[others], oracle_hashes(broken, 64, indices=others))
 
 
+@pytest.mark.parametrize("case", ["all_short", "long_last", "long_first", "all_1k", "spread"])
+def test_short_kernel_with_the_length_count(ctx, case):
+    """One key, offsets form, 20000 messages: the short kernel also counts the
+    length buckets of the sort, and hashes short messages until it meets a
+    longer one (or a thread that did has set the flag); the warp-tile kernel
+    then hashes the whole batch in sorted order.  All messages of 0..64
+    bytes; one of 65 bytes last or first among them; all of 1 KiB; lengths
+    spread over many buckets (0..5000 bytes and four of 64 KiB to 1 MiB).
+    The output starts filled with a pattern and every message is checked
+    against the oracle (a bucket miscounted would leave a message out of the
+    sorted order).  Launches: the short kernel, the scan, the scatter and the
+    two warp-tile variants."""
+    g = torch.Generator().manual_seed(97)
+    n = 20000
+    if case == "all_1k":
+        lengths = torch.full((n,), 1024)
+    elif case == "spread":
+        lengths = torch.cat([torch.randint(0, 5001, (n - 4,), generator=g),
+                             torch.tensor([1 << 16, (1 << 17) + 5, 700001, (1 << 20) + 9])])
+        lengths = lengths[torch.randperm(n, generator=g)]
+    else:
+        lengths = torch.randint(0, 65, (n,), generator=g)
+        if case != "all_short":
+            lengths[-1 if case == "long_last" else 0] = 65
+    w = workloads.from_lengths(lengths, seed=97, device=DEV, per_message_keys=False)
+    for bits, fn in ((64, hh.hh_hash64_batch), (256, hh.hh_hash256_batch)):
+        out = torch.full((n * WORDS[bits],), 0x5A5A5A5A, dtype=torch.int64, device=DEV)
+        fn(ctx, w.keys, 0, w.data, w.offsets, out=out)
+        assert hh.hh_get_device_error(ctx) == hh.HH_OK
+        assert hh.hh_last_launch_count(ctx) == 5
+        assert np.array_equal(as_u64(out, WORDS[bits]), oracle_hashes(w, bits)), (case, bits)
+
+
 def test_output_guard_words_untouched(ctx):
     w = workloads.ragged(3000, seed=11, device=DEV, max_len=3000)
     out = torch.full((3000 * 2 + 64,), -0x5A5A5A5A5A5A5A5B, dtype=torch.int64, device=DEV)
