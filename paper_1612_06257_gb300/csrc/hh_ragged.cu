@@ -833,16 +833,24 @@ __device__ __forceinline__ void set_flag(uint32_t* p) {
 // block has left the hash loop (no copy is then in flight), so the kernel
 // takes no more shared memory, and L1 no less, than short_kernel.
 // A message of at most kShortMax bytes is hashed, until the thread meets a
-// longer one or finds the flag hist[kBuckets] that a thread which met one
-// has set; from then on the thread only counts (four messages per step, the
-// offsets loaded together).  So the hash loop counts nothing.  A set flag
+// longer one (and sets the flag hist[kBuckets]) or finds the flag set; from
+// then on the thread only counts (four messages per step, the offsets loaded
+// together).  So the hash loop counts nothing, and reads the flag once per
+// kFlagChunk messages (a load per message, all to one word, cost 2% of the
+// time), issued a chunk ahead so that its latency is hidden, and not in a
+// thread's first chunk; one thread per block stores it (when every message
+// is long, every thread meets one at once).  A set flag
 // means a long message is in the histogram: the scan turns the sorted order
 // on and the warp-tile kernel hashes every message, so none skipped here
 // goes unhashed.  In an all-short batch nothing sets the flag and every
 // message is hashed here.
+constexpr uint32_t kFlagChunk = 32;
+
 template <int kWords>
 __global__ void __launch_bounds__(256, 3) short_count_kernel(Batch b, uint32_t* hist) {
-  const int64_t n = b.n;
+  // Message indices fit in 32 bits: a sorted batch has at most 2^31 - 1
+  // messages, and an index plus kFlagChunk grid strides stays below 2^32.
+  const uint32_t n = static_cast<uint32_t>(b.n);
   int64_t lo, hi;
   batch_range(b, lo, hi);
   const uintptr_t base = reinterpret_cast<uintptr_t>(b.bytes);
@@ -850,9 +858,11 @@ __global__ void __launch_bounds__(256, 3) short_count_kernel(Batch b, uint32_t* 
   __shared__ int64_t next_offsets[2][256][2];
   __shared__ uint32_t next_words[2][256 * 17];
   __shared__ __align__(16) uint64_t s_init[16];
+  __shared__ uint32_t s_told;  // the block has stored the flag
   static_assert(sizeof(next_words) >= kBuckets * sizeof(uint32_t), "histogram space");
   const int tid = threadIdx.x;
   if (tid == 0) {
+    s_told = 0;
     uint64_t key[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) key[i] = __ldg(b.keys + i);
@@ -867,7 +877,7 @@ __global__ void __launch_bounds__(256, 3) short_count_kernel(Batch b, uint32_t* 
     }
   }
   __syncthreads();
-  auto fetch_offsets = [&](int64_t mm, int slot) {
+  auto fetch_offsets = [&](uint32_t mm, int slot) {
     cp_async8(smem_u32(&next_offsets[slot][tid][0]), b.offsets + mm);
     cp_async8(smem_u32(&next_offsets[slot][tid][1]), b.offsets + mm + 1);
     cp_async_commit();
@@ -879,55 +889,66 @@ __global__ void __launch_bounds__(256, 3) short_count_kernel(Batch b, uint32_t* 
     uint32_t* dst = &next_words[slot][17 * tid];
     stage_short_words(dst, smem_u32(dst), base + s, static_cast<uint32_t>(l), base + lo, base + hi);
   };
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * 256;
-  const int64_t first_m = static_cast<int64_t>(blockIdx.x) * 256 + tid;
-  int64_t m = first_m;
+  const uint32_t stride = gridDim.x * 256u;
+  const uint32_t first_m = blockIdx.x * 256u + tid;
+  uint32_t m = first_m;
   if (m < n) {
     fetch_offsets(m, 0);
     cp_async_wait<0>();
     fetch_words(0);
   }
   int cur = 0;
+  // seen: the flag as read at the start of the chunk before, or 1 once this
+  // thread has met a long message.
   uint32_t seen = 0;
-  for (; m < n; m += stride) {
-    cp_async_wait<0>();  // this message's offsets and words are in slot cur
-    const int64_t s0 = next_offsets[cur][tid][0], e0 = next_offsets[cur][tid][1];
-    const int bad = e0 < s0 ? kErrBadOffsets : 0;
-    const int64_t len = bad ? 0 : e0 - s0;
-    if (len > kShortMax || seen != 0) break;  // m is counted below
-    const bool more = m + stride < n;
-    if (more) fetch_offsets(m + stride, cur ^ 1);
-    seen = load_flag(flag);
-    if (bad) record_error(b.err, bad);
-    State s;
-    {
-      const uint4* p = reinterpret_cast<const uint4*>(s_init);
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const uint4 a = p[i], c = p[2 + i], d = p[4 + i], e = p[6 + i];
-        s.v0[2 * i] = join(a.x, a.y);
-        s.v0[2 * i + 1] = join(a.z, a.w);
-        s.v1[2 * i] = join(c.x, c.y);
-        s.v1[2 * i + 1] = join(c.z, c.w);
-        s.mul0[2 * i] = join(d.x, d.y);
-        s.mul0[2 * i + 1] = join(d.z, d.w);
-        s.mul1[2 * i] = join(e.x, e.y);
-        s.mul1[2 * i + 1] = join(e.z, e.w);
+  while (m < n && seen == 0) {
+    if (m >= kFlagChunk * stride) seen = load_flag(flag);  // not the first chunk
+    const uint32_t end = n - m > kFlagChunk * stride ? m + kFlagChunk * stride : n;
+    for (; m < end; m += stride) {
+      cp_async_wait<0>();  // this message's offsets and words are in slot cur
+      const int64_t s0 = next_offsets[cur][tid][0], e0 = next_offsets[cur][tid][1];
+      const int bad = e0 < s0 ? kErrBadOffsets : 0;
+      const int64_t len = bad ? 0 : e0 - s0;
+      if (len > kShortMax) {  // m is counted below
+        if (atomicExch(&s_told, 1u) == 0u) set_flag(flag);
+        seen = 1;
+        break;
       }
+      const bool more = m + stride < n;
+      if (more) fetch_offsets(m + stride, cur ^ 1);
+      if (bad) record_error(b.err, bad);
+      State s;
+      {
+        const uint4* p = reinterpret_cast<const uint4*>(s_init);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const uint4 a = p[i], c = p[2 + i], d = p[4 + i], e = p[6 + i];
+          s.v0[2 * i] = join(a.x, a.y);
+          s.v0[2 * i + 1] = join(a.z, a.w);
+          s.v1[2 * i] = join(c.x, c.y);
+          s.v1[2 * i + 1] = join(c.z, c.w);
+          s.mul0[2 * i] = join(d.x, d.y);
+          s.mul0[2 * i + 1] = join(d.z, d.w);
+          s.mul1[2 * i] = join(e.x, e.y);
+          s.mul1[2 * i + 1] = join(e.z, e.w);
+        }
+      }
+      hash_short_slot(s, &next_words[cur][17 * tid], static_cast<uint32_t>((base + s0) & 3),
+                      static_cast<uint32_t>(len));
+      if (more) {
+        cp_async_wait<0>();
+        fetch_words(cur ^ 1);
+      }
+      cur ^= 1;
+      finalize(s);
+      store_short_hash<kWords>(b, m, bad, s);
     }
-    hash_short_slot(s, &next_words[cur][17 * tid], static_cast<uint32_t>((base + s0) & 3),
-                    static_cast<uint32_t>(len));
-    if (more) {
-      cp_async_wait<0>();
-      fetch_words(cur ^ 1);
-    }
-    cur ^= 1;
-    finalize(s);
-    store_short_hash<kWords>(b, m, bad, s);
   }
   // Count only, from message m on: the long ones, runs of equal buckets
   // with one shared atomic per run.  The barrier waits for the block's
-  // threads to leave the hash loop (each waited for its own copies there).
+  // threads to leave the hash loop, each with its copies landed (one that
+  // left at a chunk start has the next message's words in flight).
+  cp_async_wait<0>();
   __syncthreads();
   uint32_t* h = &next_words[0][0];
   for (int i = tid; i < kBuckets; i += 256) h[i] = 0;
@@ -935,13 +956,12 @@ __global__ void __launch_bounds__(256, 3) short_count_kernel(Batch b, uint32_t* 
   uint32_t big = 0;
   int run_key = 0;
   uint32_t run = 0;
-  bool told = false;
   for (; m < n; m += 4 * stride) {
     int64_t st[4], en[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int64_t i = m + k * stride;
-      const int64_t j = i < n ? i : n - 1;
+      const uint32_t i = m + k * stride;
+      const uint32_t j = i < n ? i : n - 1;
       st[k] = __ldg(b.offsets + j);
       en[k] = __ldg(b.offsets + j + 1);
     }
@@ -951,10 +971,6 @@ __global__ void __launch_bounds__(256, 3) short_count_kernel(Batch b, uint32_t* 
         const int64_t len = en[k] - st[k];
         if (len > kShortMax) {
           const int key = bucket_of_packets((len + 31) >> 5);
-          if (!told) {
-            set_flag(flag);
-            told = true;
-          }
           ++big;
           if (key != run_key) {
             if (run != 0) atomicAdd(&h[run_key], run);
@@ -970,8 +986,7 @@ __global__ void __launch_bounds__(256, 3) short_count_kernel(Batch b, uint32_t* 
   // Bucket 2: the thread's messages that are not long, one shared atomic
   // per warp; then the block's histogram goes to hist, one global atomic
   // per non-empty bucket.
-  const uint32_t mine =
-      first_m < n ? static_cast<uint32_t>((n - 1 - first_m) / stride + 1) : 0u;
+  const uint32_t mine = first_m < n ? (n - 1 - first_m) / stride + 1 : 0u;
   uint32_t short_count = mine - big;
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) short_count += __shfl_xor_sync(0xffffffffu, short_count, d);

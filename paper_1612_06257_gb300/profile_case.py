@@ -6,10 +6,11 @@ builds one seeded batch on cuda:0 and hashes it `--reps` times through the C
 ABI (the first launch warms up; profile with `-s 1 -c 1` to capture the
 second).  Kinds: fixed (hh_hash_fixed), ragged (log-uniform lengths,
 per-message keys), short (0..64-byte messages), long (n messages of
-`--length` bytes through the offsets form: solo or pair tiles from 128 KiB)
-siptree (n messages of `--length` bytes, SipTreeHash through
-hh_siptree_batch; --bits 13 for SipTreeHash13) and prng (n counters of
-counter mode through hh_prng_fill, --bits of output each).
+`--length` bytes through the offsets form: solo or pair tiles from 128 KiB),
+offsets (the same with one key: the short kernel counts the lengths, the
+warp-tile kernel hashes), siptree (n messages of `--length` bytes,
+SipTreeHash through hh_siptree_batch; --bits 13 for SipTreeHash13) and prng
+(n counters of counter mode through hh_prng_fill, --bits of output each).
 """
 import argparse
 
@@ -20,7 +21,8 @@ from paper_1612_06257_gb300 import hh, workloads
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("--kind", choices=["fixed", "ragged", "short", "long", "siptree", "prng"],
+    p.add_argument("--kind",
+                   choices=["fixed", "ragged", "short", "long", "offsets", "siptree", "prng"],
                    default="fixed")
     p.add_argument("--n", type=int, default=1 << 18)
     p.add_argument("--length", type=int, default=1024)
@@ -45,7 +47,7 @@ def main():
         w = workloads.fixed(a.n, a.length, seed=1, device=dev)
     elif a.kind == "ragged":
         w = workloads.ragged(a.n, seed=1, device=dev)
-    elif a.kind in ("long", "siptree"):
+    elif a.kind in ("long", "offsets", "siptree"):
         w = workloads.from_lengths([a.length] * a.n, seed=1, device=dev,
                                    per_message_keys=a.kind == "long")
     else:
