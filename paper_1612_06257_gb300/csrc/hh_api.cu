@@ -101,7 +101,7 @@ int hash_device(hh_ctx* ctx, hh::Batch b, cudaStream_t stream) {
     int launches = 0;
     cudaError_t e;
     if (counted_short) {
-      e = cudaMemsetAsync(ctx->d_hist, 0, sizeof(uint32_t) * (hh::kBuckets + 1), stream);
+      e = cudaMemsetAsync(ctx->d_hist, 0, sizeof(uint32_t) * (hh::kBuckets + 2), stream);
       if (e == cudaSuccess) e = hh::launch_short_counted(b, ctx->d_hist, ctx->num_sms, stream);
       if (e == cudaSuccess)
         e = hh::launch_bucket_scan_scatter(b, ctx->d_hist, ctx->d_cursor, ctx->d_perm,
@@ -279,7 +279,7 @@ int hh_init(hh_ctx** out, int device, const char* tune_cache_path) {
             cudaMalloc(&ctx->d_next_tile, 4 * sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&ctx->d_use_perm, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&ctx->d_huge, sizeof(long long)) == cudaSuccess &&
-            cudaMalloc(&ctx->d_hist, sizeof(uint32_t) * (hh::kBuckets + 1)) == cudaSuccess &&
+            cudaMalloc(&ctx->d_hist, sizeof(uint32_t) * (hh::kBuckets + 2)) == cudaSuccess &&
             cudaMalloc(&ctx->d_cursor, sizeof(uint32_t) * hh::kBuckets) == cudaSuccess &&
             cudaMemset(ctx->d_err, 0, sizeof(int)) == cudaSuccess &&
             cudaMemset(ctx->d_next_tile, 0, 4 * sizeof(unsigned long long)) == cudaSuccess &&

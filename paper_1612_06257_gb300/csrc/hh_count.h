@@ -22,13 +22,14 @@ inline bool short_count_eligible(const Batch& b) {
          b.stream_mode == kWholeMessages && b.n_dev == nullptr;
 }
 
-// hist: kBuckets + 1 words, zeroed by the caller.  The kernel adds every
+// hist: kBuckets + 2 words, zeroed by the caller.  The kernel adds every
 // message's length bucket to hist[0 .. kBuckets) (the buckets of
 // launch_bucket_sort's count, except that buckets 0..2, the messages of at
 // most kShortMax bytes, are all counted in bucket 2) and uses hist[kBuckets]
-// as the flag that some message is longer than kShortMax.  When no message
-// is, every hash is written; otherwise hashes may or may not be written, and
-// the warp-tile kernel launched after the scan writes them all.
+// as the flag that some message is longer than kShortMax, hist[kBuckets + 1]
+// as the counter of its work queue.  When no message is, every hash is
+// written; otherwise hashes may or may not be written, and the warp-tile
+// kernel launched after the scan writes them all.
 cudaError_t launch_short_counted(const Batch& b, uint32_t* hist, int num_sms,
                                  cudaStream_t stream);
 

@@ -824,43 +824,56 @@ __device__ __forceinline__ void set_flag(uint32_t* p) {
 }
 
 // short_kernel's one-key offsets-form loop with the length count of the
-// sort folded in (one pass over the offsets instead of two).  The count
-// merges buckets 0..2 (messages of at most kShortMax bytes, whose order
-// among themselves does not matter) into bucket 2, as the scatter of this
-// path does: a message longer than kShortMax goes to its own bucket
-// (bucket_of_packets of ceil(len / 32)), and bucket 2 gets the others.  The
-// block's histogram reuses the staged-word buffer once every thread of the
-// block has left the hash loop (no copy is then in flight), so the kernel
-// takes no more shared memory, and L1 no less, than short_kernel.
-// A message of at most kShortMax bytes is hashed, until the thread meets a
-// longer one (and sets the flag hist[kBuckets]) or finds the flag set; from
-// then on the thread only counts (four messages per step, the offsets loaded
-// together).  So the hash loop counts nothing, and reads the flag once per
-// kFlagChunk messages (a load per message, all to one word, cost 2% of the
-// time), issued a chunk ahead so that its latency is hidden, and not in a
-// thread's first chunk; one thread per block stores it (when every message
-// is long, every thread meets one at once).  A set flag
-// means a long message is in the histogram: the scan turns the sorted order
-// on and the warp-tile kernel hashes every message, so none skipped here
-// goes unhashed.  In an all-short batch nothing sets the flag and every
-// message is hashed here.
-constexpr uint32_t kFlagChunk = 32;
+// sort folded in (one pass over the offsets instead of two).
+//
+// Work: runs of kRunMsgs consecutive messages, kRun per lane (lane l takes
+// messages base + 32 j + l, so a warp's loads and stores stay coalesced).
+// A warp's two first runs follow from its index (run k of warp w is number
+// k W + w, W warps in the grid); the later ones come from a counter
+// (hist[kBuckets + 1]), each claimed a run ahead (a claim for the first run,
+// made by every warp at kernel start on one word, took 10 us of a
+// 2^20-message count).  With a fixed share per thread the warps that the
+// scheduler favoured finished early and left the SMs short of warps (17.8
+// of 24 active on average).
+//
+// Count: buckets 0..2 (messages of at most kShortMax bytes, whose order
+// among themselves does not matter) are merged into bucket 2, as the
+// scatter of this path does; a longer message goes to its own bucket
+// (bucket_of_packets of ceil(len / 32)).
+//
+// Hash: a message of at most kShortMax bytes is hashed (and tallied for
+// bucket 2) until a lane of the warp meets a longer one, which sets the flag
+// hist[kBuckets] (one store per block), or the warp finds the flag set (read
+// once per run, a run ahead, from a warp's third run on).  From then on the
+// warp only counts, four messages per lane per step with their offsets
+// loaded together.  A set flag means a long message is in the histogram:
+// the scan turns the sorted order on and the warp-tile kernel hashes every
+// message, so none skipped here goes unhashed.  In an all-short batch
+// nothing sets the flag and every message is hashed here.  The block's
+// histogram reuses the staged-word buffer once the block's threads are done
+// hashing (each with its copies landed), so the kernel takes no more shared
+// memory, and L1 no less, than short_kernel.
+constexpr uint32_t kRun = 8;
+constexpr uint32_t kRunMsgs = 32 * kRun;
+constexpr uint32_t kCountWarps = 8;  // warps per block
 
 template <int kWords>
 __global__ void __launch_bounds__(256, 3) short_count_kernel(Batch b, uint32_t* hist) {
   // Message indices fit in 32 bits: a sorted batch has at most 2^31 - 1
-  // messages, and an index plus kFlagChunk grid strides stays below 2^32.
+  // messages, and the runs handed out pass n by at most two per warp.
   const uint32_t n = static_cast<uint32_t>(b.n);
   int64_t lo, hi;
   batch_range(b, lo, hi);
   const uintptr_t base = reinterpret_cast<uintptr_t>(b.bytes);
   uint32_t* flag = hist + kBuckets;
+  uint32_t* run_counter = hist + kBuckets + 1;
   __shared__ int64_t next_offsets[2][256][2];
   __shared__ uint32_t next_words[2][256 * 17];
   __shared__ __align__(16) uint64_t s_init[16];
   __shared__ uint32_t s_told;  // the block has stored the flag
   static_assert(sizeof(next_words) >= kBuckets * sizeof(uint32_t), "histogram space");
   const int tid = threadIdx.x;
+  const uint32_t lane = tid & 31u;
   if (tid == 0) {
     s_told = 0;
     uint64_t key[4];
@@ -889,34 +902,50 @@ __global__ void __launch_bounds__(256, 3) short_count_kernel(Batch b, uint32_t* 
     uint32_t* dst = &next_words[slot][17 * tid];
     stage_short_words(dst, smem_u32(dst), base + s, static_cast<uint32_t>(l), base + lo, base + hi);
   };
-  const uint32_t stride = gridDim.x * 256u;
-  const uint32_t first_m = blockIdx.x * 256u + tid;
-  uint32_t m = first_m;
+  // A warp's two first runs go by its index (half of fixed_end apart); the
+  // counter hands out the runs from fixed_end on, each claimed a run ahead
+  // (ticket: lane 0's claim for the run after next_run).
+  const uint32_t fixed_end = 2 * gridDim.x * kCountWarps * kRunMsgs;
+  uint32_t run = (blockIdx.x * kCountWarps + (tid >> 5)) * kRunMsgs;
+  uint32_t next_run = run + fixed_end / 2;
+  uint32_t ticket = 0;
+  if (lane == 0) ticket = atomicAdd(run_counter, kRunMsgs);
+  auto advance = [&]() {
+    run = next_run;
+    next_run = fixed_end + __shfl_sync(0xffffffffu, ticket, 0);
+    if (lane == 0) ticket = atomicAdd(run_counter, kRunMsgs);
+  };
+  uint32_t m = run + lane;
+  uint32_t j = 0;
+  uint32_t hashed = 0;  // messages hashed here (all in bucket 2)
   if (m < n) {
     fetch_offsets(m, 0);
     cp_async_wait<0>();
     fetch_words(0);
   }
   int cur = 0;
-  // seen: the flag as read at the start of the chunk before, or 1 once this
-  // thread has met a long message.
-  uint32_t seen = 0;
-  while (m < n && seen == 0) {
-    if (m >= kFlagChunk * stride) seen = load_flag(flag);  // not the first chunk
-    const uint32_t end = n - m > kFlagChunk * stride ? m + kFlagChunk * stride : n;
-    for (; m < end; m += stride) {
+  uint32_t seen = 0;  // the flag as read during the run before
+  while (run < n) {
+    if (__any_sync(0xffffffffu, seen != 0)) break;  // count from step 0 of this run
+    if (run >= fixed_end) seen = load_flag(flag);  // not in the warp's fixed runs
+    bool met_long = false;
+    for (j = 0; j < kRun; ++j, m += 32) {
       cp_async_wait<0>();  // this message's offsets and words are in slot cur
+      const bool have = m < n;
       const int64_t s0 = next_offsets[cur][tid][0], e0 = next_offsets[cur][tid][1];
-      const int bad = e0 < s0 ? kErrBadOffsets : 0;
-      const int64_t len = bad ? 0 : e0 - s0;
-      if (len > kShortMax) {  // m is counted below
-        if (atomicExch(&s_told, 1u) == 0u) set_flag(flag);
-        seen = 1;
+      const int bad = have && e0 < s0 ? kErrBadOffsets : 0;
+      const int64_t len = bad || !have ? 0 : e0 - s0;
+      const bool is_long = len > kShortMax;
+      if (__any_sync(0xffffffffu, is_long)) {  // the warp counts from here on
+        if (is_long && atomicExch(&s_told, 1u) == 0u) set_flag(flag);
+        met_long = true;
         break;
       }
-      const bool more = m + stride < n;
-      if (more) fetch_offsets(m + stride, cur ^ 1);
+      const uint32_t nm = j + 1 < kRun ? m + 32 : next_run + lane;
+      const bool more = nm < n;
+      if (more) fetch_offsets(nm, cur ^ 1);
       if (bad) record_error(b.err, bad);
+      hashed += have ? 1u : 0u;
       State s;
       {
         const uint4* p = reinterpret_cast<const uint4*>(s_init);
@@ -941,56 +970,63 @@ __global__ void __launch_bounds__(256, 3) short_count_kernel(Batch b, uint32_t* 
       }
       cur ^= 1;
       finalize(s);
-      store_short_hash<kWords>(b, m, bad, s);
+      if (have) store_short_hash<kWords>(b, m, bad, s);
     }
+    if (met_long) break;  // count from step j of this run
+    advance();
+    m = run + lane;
+    j = 0;
   }
-  // Count only, from message m on: the long ones, runs of equal buckets
-  // with one shared atomic per run.  The barrier waits for the block's
-  // threads to leave the hash loop, each with its copies landed (one that
-  // left at a chunk start has the next message's words in flight).
+  // Count only: this run from step j on (message m, not counted yet), then
+  // the runs that follow.  Runs of equal buckets go to the block histogram
+  // with one shared atomic per run; it takes the staged-word buffer once
+  // every thread of the block is done with it.
   cp_async_wait<0>();
   __syncthreads();
   uint32_t* h = &next_words[0][0];
   for (int i = tid; i < kBuckets; i += 256) h[i] = 0;
   __syncthreads();
-  uint32_t big = 0;
+  uint32_t short_count = hashed;
   int run_key = 0;
-  uint32_t run = 0;
-  for (; m < n; m += 4 * stride) {
-    int64_t st[4], en[4];
+  uint32_t same = 0;
+  while (run < n) {
+    for (; j < kRun; j += 4, m += 128) {
+      int64_t st[4], en[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint32_t i = m + k * stride;
-      const uint32_t j = i < n ? i : n - 1;
-      st[k] = __ldg(b.offsets + j);
-      en[k] = __ldg(b.offsets + j + 1);
-    }
+      for (uint32_t q = 0; q < 4; ++q) {
+        const uint32_t i = m + 32 * q;
+        const uint32_t k = i < n ? i : n - 1;
+        st[q] = __ldg(b.offsets + k);
+        en[q] = __ldg(b.offsets + k + 1);
+      }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (m + k * stride < n) {
-        const int64_t len = en[k] - st[k];
-        if (len > kShortMax) {
-          const int key = bucket_of_packets((len + 31) >> 5);
-          ++big;
-          if (key != run_key) {
-            if (run != 0) atomicAdd(&h[run_key], run);
-            run_key = key;
-            run = 0;
+      for (uint32_t q = 0; q < 4; ++q) {
+        if (j + q < kRun && m + 32 * q < n) {
+          const int64_t len = en[q] - st[q];
+          if (len > kShortMax) {
+            const int key = bucket_of_packets((len + 31) >> 5);
+            if (key != run_key) {
+              if (same != 0) atomicAdd(&h[run_key], same);
+              run_key = key;
+              same = 0;
+            }
+            ++same;
+          } else {
+            ++short_count;
           }
-          ++run;
         }
       }
     }
+    advance();
+    m = run + lane;
+    j = 0;
   }
-  if (run != 0) atomicAdd(&h[run_key], run);
-  // Bucket 2: the thread's messages that are not long, one shared atomic
-  // per warp; then the block's histogram goes to hist, one global atomic
-  // per non-empty bucket.
-  const uint32_t mine = first_m < n ? (n - 1 - first_m) / stride + 1 : 0u;
-  uint32_t short_count = mine - big;
+  if (same != 0) atomicAdd(&h[run_key], same);
+  // Bucket 2, one shared atomic per warp; then the block's histogram goes
+  // to hist, one global atomic per non-empty bucket.
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) short_count += __shfl_xor_sync(0xffffffffu, short_count, d);
-  if ((tid & 31) == 0 && short_count != 0) atomicAdd(&h[2], short_count);
+  if (lane == 0 && short_count != 0) atomicAdd(&h[2], short_count);
   __syncthreads();
   for (int i = tid; i < kBuckets; i += 256)
     if (h[i] != 0) atomicAdd(&hist[i], h[i]);
@@ -1050,11 +1086,11 @@ cudaError_t launch_short_counted(const Batch& b, uint32_t* hist, int num_sms,
   cudaError_t e;
   const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), 256, 0, &e);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = (b.n + 255) / 256;
+  const int64_t blocks = (b.n + kCountWarps * kRunMsgs - 1) / (kCountWarps * kRunMsgs);
   const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
   const int grid = static_cast<int>(blocks < cap ? blocks : cap);
   if (grid <= 0) return cudaSuccess;
-  kern<<<grid, 256, 0, stream>>>(b, hist);
+  kern<<<grid, kCountWarps * 32, 0, stream>>>(b, hist);
   return cudaGetLastError();
 }
 
