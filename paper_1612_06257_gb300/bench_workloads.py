@@ -231,6 +231,28 @@ def short(ctx, dev):
             naive = _naive_ms(ctx, lambda: fn(ctx, w.keys, 0, w.data, w.offsets, out=out), 5)
             res["naive_hashes_per_s_64"] = round(w.n / (naive / 1e3), 1)
             res["speedup_vs_naive_64"] = round(naive / ms, 2)
+    res["one_long_message"] = _short_with_one_long(ctx, w)
+    return res
+
+
+def _short_with_one_long(ctx, w):
+    """ms per 64-bit call of the same batch with one message made 65 bytes
+    long (first, in the middle or last): the short kernel meets it when it
+    gets there, and the warp-tile kernel then hashes the whole batch."""
+    lengths = w.offsets[1:] - w.offsets[:-1]
+    data = torch.cat([w.data, torch.zeros(128, dtype=torch.uint8, device=w.data.device)])
+    out = torch.empty(w.n, dtype=torch.int64, device=w.data.device)
+    res = {}
+    for where, i in (("none", None), ("first", 0), ("middle", w.n // 2), ("last", w.n - 1)):
+        ln = lengths.clone()
+        if i is not None:
+            ln[i] = 65
+        off = torch.zeros_like(w.offsets)
+        off[1:] = torch.cumsum(ln, 0)
+        ms, _ = _time(lambda: hh.hh_hash64_batch(ctx, w.keys, 0, data, off, out=out), 5)
+        res[where + "_ms"] = round(ms, 3)
+    res["note"] = ("one-key batch of 2^26 messages of 0..64 B with one message of 65 B; "
+                   "with the length count in a launch of its own every case took about 4.1 ms")
     return res
 
 
