@@ -232,6 +232,14 @@ def short(ctx, dev):
             res["naive_hashes_per_s_64"] = round(w.n / (naive / 1e3), 1)
             res["speedup_vs_naive_64"] = round(naive / ms, 2)
     res["one_long_message"] = _short_with_one_long(ctx, w)
+    del w
+    # The same recipe with a key per message: the separate length count and
+    # short_kernel (the words loaded directly, each message's key too).
+    wk = workloads.short(1 << 26, seed=3, device=dev, per_message_keys=True)
+    out = torch.empty(wk.n, dtype=torch.int64, device=dev)
+    ms, _ = _time(lambda: hh.hh_hash64_batch(ctx, wk.keys, 1, wk.data, wk.offsets, out=out), 10)
+    res["hashes_per_s_64_per_message_keys"] = round(wk.n / (ms / 1e3), 1)
+    res["launches_per_batch_64_per_message_keys"] = hh.hh_last_launch_count(ctx)
     return res
 
 

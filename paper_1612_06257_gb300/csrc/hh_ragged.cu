@@ -674,10 +674,12 @@ __device__ __forceinline__ void store_short_hash(const Batch& b, int64_t m, int 
 }
 
 // Thread per message for batches whose messages are all at most kShortMax
-// bytes, in index order (neighbouring threads read neighbouring bytes).
-// Three blocks of 256 threads per SM (80 registers).  kWords: the output
-// width in words, fixed per instantiation for whole messages (0 in the
-// stream instantiation, which reads it at run time).
+// bytes, other than the one-key offsets-form batches that short_count_kernel
+// takes: a key per message, a key table, segments and streams.  In index
+// order (neighbouring threads read neighbouring bytes), three blocks of 256
+// threads per SM (80 registers).  kWords: the output width in words, fixed
+// per instantiation for whole messages (0 in the stream instantiation, which
+// reads it at run time).
 template <bool kStream, int kWords>
 __global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, const int* run_if) {
   if (run_if != nullptr && *run_if != 0) return;
@@ -685,12 +687,6 @@ __global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, co
   int64_t lo, hi;
   batch_range(b, lo, hi);
   const uintptr_t base = reinterpret_cast<uintptr_t>(b.bytes);
-  uint64_t key[4];
-  const bool shared_key = !kStream && !b.per_message_keys && b.key_index == nullptr;
-  if (shared_key) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) key[i] = __ldg(b.keys + i);
-  }
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t first_m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (kStream || b.offsets == nullptr || b.key_index != nullptr) {
@@ -707,105 +703,35 @@ __global__ void __launch_bounds__(256, kStream ? 2 : 3) short_kernel(Batch b, co
     }
     return;
   }
-  // Offsets form, pipelined one message ahead through shared memory: at the
-  // start of a message the thread copies the next message's two offsets, so
-  // that no message waits for its offsets.  With one key for the batch the
-  // thread also copies the next message's 17 words after this message's
-  // data packets; they land during the four finalisation rounds, and a
-  // message then waits for no global load at all.  (With a key per message
-  // the words are loaded directly: there the key load is waited for anyway,
-  // and staging the words measured slower.)  A word slot is 17 words (an odd
-  // stride: a warp's reads of one word hit 32 different banks).
+  // Offsets form, pipelined one message ahead: at the start of a message the
+  // thread copies the next message's two offsets into shared memory, so that
+  // no message waits for its offsets.  The words are loaded directly: the
+  // key load is waited for anyway, and staging the words measured slower.
   __shared__ int64_t next_offsets[2][256][2];
-  __shared__ uint32_t next_words[2][256 * 17];
   const int tid = threadIdx.x;
   auto fetch_offsets = [&](int64_t mm, int slot) {
     cp_async8(smem_u32(&next_offsets[slot][tid][0]), b.offsets + mm);
     cp_async8(smem_u32(&next_offsets[slot][tid][1]), b.offsets + mm + 1);
     cp_async_commit();
   };
-  if (!shared_key) {
-    if (first_m < b.n) fetch_offsets(first_m, 0);
-    int cur = 0;
-    for (int64_t m = first_m; m < b.n; m += stride) {
-      cp_async_wait<0>();
-      const int64_t s0 = next_offsets[cur][tid][0], e0 = next_offsets[cur][tid][1];
-      if (m + stride < b.n) fetch_offsets(m + stride, cur ^ 1);
-      cur ^= 1;
-      const int bad = e0 < s0 ? kErrBadOffsets : 0;
-      int64_t len = bad ? 0 : e0 - s0;
-      len = len < kShortMax ? len : kShortMax;
-      if (bad) record_error(b.err, bad);
-      const uint64_t* kp = key_of(b, m);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
-      State s;
-      init(s, key);
-      hash_short(s, base + s0, static_cast<uint32_t>(len), base + lo, base + hi);
-      finalize(s);
-      store_short_hash<kWords>(b, m, bad, s);
-    }
-    return;
-  }
-  // The initial state is the same for every message of a one-key batch:
-  // built once per block in shared memory, read back with broadcast loads.
-  __shared__ __align__(16) uint64_t s_init[16];
-  if (tid == 0) {
-    State s0;
-    init(s0, key);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      s_init[i] = s0.v0[i];
-      s_init[4 + i] = s0.v1[i];
-      s_init[8 + i] = s0.mul0[i];
-      s_init[12 + i] = s0.mul1[i];
-    }
-  }
-  __syncthreads();
-  auto fetch_words = [&](int slot) {  // the slot's offsets have landed
-    const int64_t s = next_offsets[slot][tid][0], e = next_offsets[slot][tid][1];
-    int64_t l = e < s ? 0 : e - s;
-    l = l < kShortMax ? l : kShortMax;
-    uint32_t* dst = &next_words[slot][17 * tid];
-    stage_short_words(dst, smem_u32(dst), base + s, static_cast<uint32_t>(l), base + lo, base + hi);
-  };
-  if (first_m >= b.n) return;
-  fetch_offsets(first_m, 0);
-  cp_async_wait<0>();
-  fetch_words(0);
+  if (first_m < b.n) fetch_offsets(first_m, 0);
   int cur = 0;
   for (int64_t m = first_m; m < b.n; m += stride) {
-    cp_async_wait<0>();  // this message's offsets and words are in slot cur
+    cp_async_wait<0>();
     const int64_t s0 = next_offsets[cur][tid][0], e0 = next_offsets[cur][tid][1];
+    if (m + stride < b.n) fetch_offsets(m + stride, cur ^ 1);
+    cur ^= 1;
     const int bad = e0 < s0 ? kErrBadOffsets : 0;
     int64_t len = bad ? 0 : e0 - s0;
     len = len < kShortMax ? len : kShortMax;
-    const bool more = m + stride < b.n;
-    if (more) fetch_offsets(m + stride, cur ^ 1);
     if (bad) record_error(b.err, bad);
-    State s;
-    {
-      const uint4* p = reinterpret_cast<const uint4*>(s_init);
+    const uint64_t* kp = key_of(b, m);
+    uint64_t key[4];
 #pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const uint4 a = p[i], c = p[2 + i], d = p[4 + i], e = p[6 + i];
-        s.v0[2 * i] = join(a.x, a.y);
-        s.v0[2 * i + 1] = join(a.z, a.w);
-        s.v1[2 * i] = join(c.x, c.y);
-        s.v1[2 * i + 1] = join(c.z, c.w);
-        s.mul0[2 * i] = join(d.x, d.y);
-        s.mul0[2 * i + 1] = join(d.z, d.w);
-        s.mul1[2 * i] = join(e.x, e.y);
-        s.mul1[2 * i + 1] = join(e.z, e.w);
-      }
-    }
-    hash_short_slot(s, &next_words[cur][17 * tid], static_cast<uint32_t>((base + s0) & 3),
-                    static_cast<uint32_t>(len));
-    if (more) {
-      cp_async_wait<0>();
-      fetch_words(cur ^ 1);
-    }
-    cur ^= 1;
+    for (int i = 0; i < 4; ++i) key[i] = __ldg(kp + i);
+    State s;
+    init(s, key);
+    hash_short(s, base + s0, static_cast<uint32_t>(len), base + lo, base + hi);
     finalize(s);
     store_short_hash<kWords>(b, m, bad, s);
   }
@@ -1070,8 +996,13 @@ cudaError_t launch_short(const Batch& b, const int* run_if, int num_sms, cudaStr
   cudaError_t e;
   const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), 256, 0, &e);
   if (e != cudaSuccess) return e;
+  // At least one full wave, and at most 64 messages per thread: with one
+  // wave and a fixed share per thread, the blocks the scheduler favoured
+  // finished early and left SMs short of warps (a 2^26-message batch with a
+  // key per message: 31.9 against 35.0 G hashes/s); later waves fill in.
   const int64_t blocks = (b.n + 255) / 256;
-  const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
+  const int64_t wave = static_cast<int64_t>(per_sm) * num_sms;
+  const int64_t cap = wave > (b.n + 256 * 64 - 1) / (256 * 64) ? wave : (b.n + 256 * 64 - 1) / (256 * 64);
   const int grid = static_cast<int>(blocks < cap ? blocks : cap);
   if (grid <= 0) return cudaSuccess;
   kern<<<grid, 256, 0, stream>>>(b, run_if);
