@@ -423,13 +423,7 @@ cudaError_t launch_fixed_t(const CUtensorMap& tmap, const FixedParams& p, int nu
   const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kern), kRows, L::kBytes, &e);
   if (e != cudaSuccess) return e;
   const int64_t tiles = (p.n + kRows * M - 1) / (kRows * M);
-  // One tile per CTA when a tile holds at least 128 KiB: the block scheduler
-  // then evens out the CTAs' finishing times (2^20 x 1 KiB: +2.2% against a
-  // persistent grid of one wave, where the CTAs the scheduler favoured
-  // finished early).  Smaller tiles keep the persistent grid, which pays a
-  // CTA's start once.
-  int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
-  if (p.len * kRows * M >= (int64_t(128) << 10) && tiles > cap) cap = tiles;
+  const int64_t cap = static_cast<int64_t>(per_sm) * num_sms;
   const int grid = static_cast<int>(tiles < cap ? tiles : cap);
   kern<<<grid, kRows, L::kBytes, stream>>>(tmap, p);
   return cudaGetLastError();
